@@ -1,0 +1,167 @@
+"""CPU FP64 oracle for the multi-RHS pressure-Poisson hot path (arXiv 1711.10622).
+
+TEST INFRASTRUCTURE. This package is the plain, slow, obviously correct reference the CUDA
+path is checked against. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import it. It shares no code with the CUDA library: the arithmetic lives in
+``oracle.c`` (compiled with gcc, FP64, no FMA contraction) and in ``estimates.py`` (the paper's
+closed-form performance model, Section 2.3).
+
+Parity pins (see tests/test_oracle_pins.py): closed-form eigenpairs of the 7-point operator,
+dense products on tiny grids, a textbook LU solve, Krylov termination on k-mode right-hand
+sides, the Chebyshev scalar polynomial on Fourier modes, and the printed estimate columns of
+Tables 4 and 5.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+from . import estimates  # noqa: F401  (re-exported)
+
+CONVERGED, MAXITER, BREAKDOWN, NONFINITE, INCOMPATIBLE = 0, 1, 2, 3, 4
+
+_lib = None
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [
+        ("max_iter", ctypes.c_int),
+        ("precond", ctypes.c_int),
+        ("cheb_steps", ctypes.c_int),
+        ("cheb_lo", ctypes.c_double),
+        ("cheb_hi", ctypes.c_double),
+        ("singular", ctypes.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.oracle_spmv.argtypes = [_i64, _vp, _vp, _vp, _vp, _i64, _vp, _i64]
+        L.oracle_gspmv.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+        L.oracle_chebyshev.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.oracle_bicgstab.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_Opts), _vp, _vp]
+        L.oracle_bicgstab.restype = ctypes.c_int
+        L.oracle_solve_block.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _vp]
+        L.oracle_lu_solve.argtypes = [ctypes.c_int, _vp, _vp]
+        L.oracle_lu_solve.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+def _csr(A):
+    row = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    val = np.ascontiguousarray(A.val, dtype=np.float64)
+    return row, col, val
+
+
+def spmv(A, x: np.ndarray) -> np.ndarray:
+    """y = A x for one vector (Section 2.3, Fig. GSpMV with m = 1)."""
+    row, col, val = _csr(A)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(A.n, dtype=np.float64)
+    lib().oracle_spmv(A.n, _p(row), _p(col), _p(val), _p(x), 1, _p(y), 1)
+    return y
+
+
+def gspmv(A, X: np.ndarray) -> np.ndarray:
+    """Y = A X for an n x m row-interleaved block, column by column (Section 2.3)."""
+    row, col, val = _csr(A)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    m = X.shape[1]
+    Y = np.empty_like(X)
+    lib().oracle_gspmv(A.n, _p(row), _p(col), _p(val), m, _p(X), _p(Y))
+    return Y
+
+
+DEFAULT_CHEB_HI = 2.0
+DEFAULT_CHEB_LO = 2.0 / 30.0
+DEFAULT_CHEB_STEPS = 4
+
+
+def chebyshev(A, r: np.ndarray, lo=DEFAULT_CHEB_LO, hi=DEFAULT_CHEB_HI, steps=DEFAULT_CHEB_STEPS):
+    """z = p(D^-1 A) D^-1 r, Chebyshev iteration from zero (Saad 2003, Alg. 12.1)."""
+    row, col, val = _csr(A)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    z = np.empty(A.n, dtype=np.float64)
+    lib().oracle_chebyshev(A.n, _p(row), _p(col), _p(val), _p(r), _p(z), lo, hi, steps)
+    return z
+
+
+def _opts(max_iter, precond, singular, cheb_lo, cheb_hi, cheb_steps):
+    return _Opts(
+        max_iter=max_iter,
+        precond={"none": 0, "chebyshev": 1}[precond],
+        cheb_steps=cheb_steps,
+        cheb_lo=cheb_lo,
+        cheb_hi=cheb_hi,
+        singular=int(bool(singular)),
+    )
+
+
+def solve_block(
+    A,
+    B: np.ndarray,
+    tol,
+    X0: np.ndarray | None = None,
+    max_iter: int = 10000,
+    precond: str = "none",
+    singular: bool | None = None,
+    cheb_lo=DEFAULT_CHEB_LO,
+    cheb_hi=DEFAULT_CHEB_HI,
+    cheb_steps=DEFAULT_CHEB_STEPS,
+):
+    """m independent BiCGStab solves A x_l = b_l (Section 2.2 / 4.1).
+
+    Returns (X, iters[m], relres[m], status[m]); relres is the true residual at exit.
+    """
+    row, col, val = _csr(A)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, m = B.shape
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, order="C", copy=True)
+    tolv = np.broadcast_to(np.asarray(tol, dtype=np.float64), (m,)).copy()
+    iters = np.zeros(m, dtype=np.int32)
+    relres = np.zeros(m, dtype=np.float64)
+    status = np.zeros(m, dtype=np.int32)
+    sing = A.singular if singular is None else singular
+    o = _opts(max_iter, precond, sing, cheb_lo, cheb_hi, cheb_steps)
+    lib().oracle_solve_block(
+        n, _p(row), _p(col), _p(val), m, _p(B), _p(X), _p(tolv), ctypes.byref(o), _p(iters), _p(relres), _p(status)
+    )
+    return X, iters, relres, status
+
+
+def lu_solve(Adense: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Dense LU with partial pivoting (textbook) on a copy of Adense."""
+    a = np.array(Adense, dtype=np.float64, order="C", copy=True)
+    x = np.array(b, dtype=np.float64, copy=True)
+    if lib().oracle_lu_solve(a.shape[0], _p(a), _p(x)) != 0:
+        raise np.linalg.LinAlgError("zero pivot")
+    return x
+
+
+def relerr_rows(Y: np.ndarray, Yref: np.ndarray, A, X: np.ndarray) -> float:
+    """max_l ||Y_l - Yref_l||_inf / || |A| |X_l| ||_inf: the GSpMV error scale per column."""
+    absA = A.to_scipy().copy()
+    absA.data = np.abs(absA.data)
+    scale = np.abs(absA @ np.abs(np.asarray(X).reshape(A.n, -1))).max(axis=0)
+    err = np.abs(np.asarray(Y).reshape(A.n, -1) - np.asarray(Yref).reshape(A.n, -1)).max(axis=0)
+    scale = np.where(scale == 0, 1.0, scale)
+    return float((err / scale).max()) if err.size else 0.0
