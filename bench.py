@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-RHS pressure-Poisson hot path on one GB300 (or N replicas).
+
+One step = one GSpMV sweep Y = A X over m in {1, 2, 4, 8, 16, 32} (FP64, Section 2.3) on the
+variable-coefficient channel operator 256 x 128 x 128 (n = 4,194,304, nnz = 29,294,592), with
+all inputs resident in HBM. `value` is the sweep's algorithmic HBM throughput:
+    bytes(m) = 4(n+1) + 12 nnz + 16 m n      (matrix once, X in once, Y out once)
+summed over the sweep, divided by the device time (CUDA events, max over ranks). Every launch
+moves >= 435 MB, more than the 129 MB L2, so no flush is needed between launches.
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on the host instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GSpMV HBM GB/s vs m; multi-RHS Poisson solves/s at rel.res 1e-8; p99 latency"
+WORKLOAD = "channel256x128x128"
+M_SWEEP = (1, 2, 4, 8, 16, 32)
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "gspmv_split_channel256x128x128.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1711_10622_gb300", "csrc", "gspmv.cu")
+
+
+def alg_bytes(n: int, nnz: int, m: int, sv: int = 8, sx: int = 8) -> int:
+    """Matrix once (row_ptr, col_idx, val), X read once, Y written once."""
+    return 4 * (n + 1) + (4 + sv) * nnz + 2 * sx * m * n
+
+
+def paper_traffic(n: int, nnz: int, m: int) -> float:
+    """Sigma_m of Section 2.3 (X re-read for every nonzero)."""
+    return 4.0 * n * (2 * m + 1) + 12.0 * nnz + 8.0 * m * nnz
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        src_hash = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not h or not t or h.group(1) != src_hash:
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    QUERY = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
+                text=True,
+            )
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+def cpu_baseline_sweep(op, seconds_cap: float = 30.0):
+    """The oracle (serial C, FP64) on the host: one full m-sweep on the full channel operator."""
+    import numpy as np
+
+    import gen
+    import oracle
+
+    n, nnz = op.n, op.nnz
+    total_bytes, total_t = 0, 0.0
+    done = []
+    for m in M_SWEEP:
+        X = gen.rhs_normal(n, m, 20000 + m)
+        t0 = time.perf_counter()
+        oracle.gspmv(op, X)
+        total_t += time.perf_counter() - t0
+        total_bytes += alg_bytes(n, nnz, m)
+        done.append(m)
+        if total_t > seconds_cap:
+            break
+        del X
+    _ = np
+    return {
+        "value": total_bytes / total_t / 1e9,
+        "unit": "GB/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"one FP64 GSpMV per m in {done} on the full {WORKLOAD} operator (serial C oracle, column by column)",
+    }
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on a bounded row sample of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import gen
+    import oracle
+
+    op = gen.channel(256, 128, 128)
+    rows = np.arange(0, op.n // 128)  # 32,768 contiguous rows (one x-y plane)
+    view = oracle.rows_view(op, rows)
+    sub_nnz = int(view[0][-1])
+    Xs = {m: gen.rhs_normal(op.n, m, 20000 + m) for m in M_SWEEP}
+
+    def step():
+        for m in M_SWEEP:
+            oracle.gspmv_csr(view, Xs[m])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    bytes_step = sum(alg_bytes(len(rows), sub_nnz, m) for m in M_SWEEP)
+    value = bytes_step * args.steps / dt / 1e9
+    sample = f"rows 0..{len(rows) - 1} ({len(rows)} of {op.n}) of the {WORKLOAD} operator, one FP64 GSpMV per m in {list(M_SWEEP)} per step"
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "GB/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} GSpMV sweep m={list(M_SWEEP)} (row sample)", "rows": len(rows), "nnz": sub_nnz},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--f64-mode", default="auto", choices=["auto", "native", "split"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import gen
+    from paper_1711_10622_gb300 import build as ens_build
+
+    ens_build.build()
+    import paper_1711_10622_gb300 as ens
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    op = gen.channel(256, 128, 128)
+    n, nnz = op.n, op.nnz
+    A = ens.Matrix.from_operator(op)
+    A.set_f64_mode(args.f64_mode)
+    stream = torch.cuda.current_stream()
+    Xs, Ys = {}, {}
+    for m in M_SWEEP:
+        Xs[m] = torch.from_numpy(gen.rhs_normal(n, m, 20000 + m)).to("cuda")
+        Ys[m] = torch.empty_like(Xs[m])
+
+    def step(evs=None):
+        for m in M_SWEEP:
+            if evs is not None:
+                evs[m][0].record(stream)
+            ens.gspmv(A, Xs[m], Ys[m], stream=stream)
+            if evs is not None:
+                evs[m][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    K = args.steps
+    evs = [{m: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for m in M_SWEEP} for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.25)
+    start.record(stream)
+    for k in range(K):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_m_us = {m: 1e3 * statistics.fmean(e[m][0].elapsed_time(e[m][1]) for e in evs) for m in M_SWEEP}
+    bytes_step = sum(alg_bytes(n, nnz, m) for m in M_SWEEP)
+    value = world * bytes_step * K / (ms * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+
+    # Dominant kernel: the m = 32 launch (largest share of the step).
+    dom_m = max(M_SWEEP, key=lambda m: per_m_us[m])
+    achieved = alg_bytes(n, nnz, dom_m) / (per_m_us[dom_m] * 1e-6) / 1e9
+    traffic = profiled_traffic() if dom_m == 32 else None
+    roofline = {
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": achieved / peak,
+        "traffic": traffic,
+        "kernel": f"gspmv m={dom_m} FP64 ({args.f64_mode})",
+        "peak_kind": peak_kind,
+    }
+    sweep = {
+        str(m): {
+            "us": per_m_us[m],
+            "gbs": alg_bytes(n, nnz, m) / (per_m_us[m] * 1e-6) / 1e9,
+            "frac_of_measured_peak": alg_bytes(n, nnz, m) / (per_m_us[m] * 1e-6) / 1e9 / peak,
+            "alg_mb": alg_bytes(n, nnz, m) / 1e6,
+            "paper_sigma_mb": paper_traffic(n, nnz, m) / 1e6,
+            "gain_vs_m1": m * per_m_us[1] / per_m_us[m],
+        }
+        for m in M_SWEEP
+    }
+
+    # End to end through the C ABI with host buffers (copies inside the timed region).
+    KE = max(1, min(args.e2e_steps, K))
+    hx = {m: torch.from_numpy(gen.rhs_normal(n, m, 30000 + m)).pin_memory().numpy() for m in M_SWEEP}
+    hy = {m: torch.empty((n, m), dtype=torch.float64).pin_memory().numpy() for m in M_SWEEP}
+    for m in M_SWEEP:  # warm the staging buffers
+        ens.gspmv_host(A, hx[m], hy[m], stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(KE):
+        for m in M_SWEEP:
+            ens.gspmv_host(A, hx[m], hy[m], stream=stream)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    io_bytes = sum(8 * n * m for m in M_SWEEP)
+    e2e = {
+        "value": world * bytes_step * KE / te / 1e9,
+        "unit": "GB/s",
+        "h2d_bytes_per_step": io_bytes,
+        "d2h_bytes_per_step": io_bytes,
+        "steps": KE,
+        "api": "ens_gspmv_host (pinned host X/Y)",
+    }
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sweep(op)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "GB/s",
+            "n_gpus": world,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": ms / K,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {
+                "workload": f"{WORKLOAD} GSpMV sweep m={list(M_SWEEP)}",
+                "n": n,
+                "nnz": nnz,
+                "f64_arithmetic": args.f64_mode,
+                "l2": "no flush: every launch streams >= 435 MB (> 129 MB L2)",
+                "parallelism": f"{world} independent replica(s)",
+            },
+            "roofline": roofline,
+            "sweep": sweep,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": K * len(M_SWEEP),
+        }
+        print(json.dumps(line))
+    A.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

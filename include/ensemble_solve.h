@@ -1,0 +1,115 @@
+/*
+ * ensemble_solve.h - C ABI of libensemble_solve.so, the GB300 (sm_103a) hot path of the
+ * multiple-ensemble method of Krasnopolsky, arXiv 1711.10622: pressure-Poisson solves for m
+ * simultaneous flow realizations that share one sparse matrix.
+ *
+ * Conventions used by every entry point
+ *   - Blocks of m vectors (X, Y, B, solutions) are n x m, stored row-wise in one array, element
+ *     (k, l) at index k*m + l ("row-interleaved"; Section 2.3, the storage assumed by Fig. GSpMV).
+ *   - CSR matrices use int32 row pointers and column indices and float64 values (Section 2.3).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Unless stated
+ *     otherwise a call only enqueues work on that stream and returns.
+ *   - Device pointers are owned by the caller and must stay valid until the enqueued work ends.
+ *     The library owns what it allocates (matrix copies, workspaces) and frees it in
+ *     ens_destroy_matrix.
+ *   - Errors: every call returns an ens_status; on failure nothing is enqueued and a message is
+ *     available from ens_last_error() (per host thread). Sizes and pointers are validated on the
+ *     host before any launch.
+ *   - One ens_matrix may be used from one host thread at a time (its workspaces are shared).
+ */
+#ifndef ENSEMBLE_SOLVE_H
+#define ENSEMBLE_SOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ens_matrix ens_matrix;
+
+typedef enum {
+  ENS_OK = 0,
+  ENS_ERR_INVALID = 1,     /* bad argument: size, pointer, CSR structure, unsupported m */
+  ENS_ERR_OOM = 2,         /* device allocation failed */
+  ENS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  ENS_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+  ENS_ERR_BUDGET = 5,      /* the request does not fit the memory budget */
+  ENS_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} ens_status;
+
+/* Per-column outcome of a solve; the numeric values are part of the ABI. */
+typedef enum {
+  ENS_COL_CONVERGED = 0,   /* ||b - A x||_2 / ||b||_2 <= tol (b = 0 gives x = 0, 0 iterations) */
+  ENS_COL_MAXITER = 1,     /* iteration limit reached */
+  ENS_COL_BREAKDOWN = 2,   /* BiCGStab breakdown: rho ~ 0, (rhat, v) = 0 or (t, t) = 0 */
+  ENS_COL_NONFINITE = 3,   /* NaN/Inf met in b, x0 or the iteration */
+  ENS_COL_INCOMPATIBLE = 4 /* singular operator and sum(b) != 0 */
+} ens_col_status;
+
+typedef enum { ENS_F64 = 0, ENS_F32 = 1 } ens_dtype;
+
+/* ens_create_matrix flags */
+#define ENS_MATRIX_SINGULAR 0x1u /* constants span the null space (pure Neumann/periodic) */
+
+/* FP64 GSpMV arithmetic (ens_set_f64_mode): how the float64 path computes its products. */
+typedef enum {
+  ENS_F64_AUTO = 0,   /* library choice (split-float arithmetic where values allow) */
+  ENS_F64_NATIVE = 1, /* native double-precision FMA for every product */
+  ENS_F64_SPLIT = 2   /* double-float products on the FP32 pipe, native FP64 fallback per row
+                         segment whose values fall outside the split range */
+} ens_f64_mode;
+
+/*
+ * Create a device-resident CSR matrix from HOST arrays (copied; the caller keeps ownership).
+ *   n        rows = columns, 1 <= n <= 2^31 - 1
+ *   nnz      nonzeros, 0 <= nnz <= 2^31 - 1
+ *   row_ptr  int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz
+ *   col_idx  int32[nnz], 0 <= col_idx[j] < n
+ *   val      float64[nnz]
+ *   flags    ENS_MATRIX_SINGULAR or 0
+ * The library also keeps a float32 copy of val (for ENS_F32 products), the inverse diagonal
+ * (Jacobi scaling of the Chebyshev preconditioner) and a split-float copy of val.
+ * Synchronous: returns after the copies end. *out receives the handle.
+ * Errors: ENS_ERR_INVALID (structure), ENS_ERR_OOM, ENS_ERR_CUDA.
+ */
+ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                             const double *val, uint32_t flags, void *stream, ens_matrix **out);
+
+/* Free the matrix and every workspace it owns. Synchronises the device first. NULL is a no-op. */
+ens_status ens_destroy_matrix(ens_matrix *A);
+
+/* n, nnz and the largest row length of A (any pointer may be NULL). */
+ens_status ens_matrix_info(const ens_matrix *A, int64_t *n, int64_t *nnz, int32_t *max_row_len);
+
+/* Select the FP64 GSpMV arithmetic for A (default ENS_F64_AUTO). */
+ens_status ens_set_f64_mode(ens_matrix *A, int32_t mode);
+
+/*
+ * Generalised SpMV Y = A X (Section 2.3, Fig. GSpMV): for every row i and column l,
+ *   Y[i*m + l] = sum_{j = row_ptr[i]}^{row_ptr[i+1]-1} val[j] * X[col_idx[j]*m + l].
+ * m >= 1 columns (any m; m in {1,2,4,8,16,32} have specialised kernels). X and Y are DEVICE
+ * pointers to n*m elements of the dtype (float64 for ENS_F64, float32 for ENS_F32; ENS_F32 uses
+ * the float32 copy of val). X and Y must not overlap. Asynchronous on `stream`.
+ * Accuracy (ENS_F64): each output is within 1e-12 of the exact sum relative to sum_j |val||x|.
+ */
+ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream);
+
+/*
+ * The same product with HOST buffers X (n*m, read) and Y (n*m, written). The library copies X to
+ * a device staging buffer it owns, runs ens_gspmv and copies Y back; synchronous (returns after
+ * Y is written). Page-locked host memory gives the full copy bandwidth.
+ */
+ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream);
+
+/* Human-readable message of the last failed call on this host thread ("" if none). */
+const char *ens_last_error(void);
+
+/* Library version string. */
+const char *ens_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENSEMBLE_SOLVE_H */

@@ -165,3 +165,36 @@ def relerr_rows(Y: np.ndarray, Yref: np.ndarray, A, X: np.ndarray) -> float:
     err = np.abs(np.asarray(Y).reshape(A.n, -1) - np.asarray(Yref).reshape(A.n, -1)).max(axis=0)
     scale = np.where(scale == 0, 1.0, scale)
     return float((err / scale).max()) if err.size else 0.0
+
+
+def rows_view(A, rows):
+    """CSR arrays (row_ptr, col_idx, val) of the rows ``rows`` of A, columns unchanged."""
+    rows = np.asarray(rows, dtype=np.int64)
+    rp = np.asarray(A.row_ptr, dtype=np.int64)
+    starts, ends = rp[rows], rp[rows + 1]
+    lens = ends - starts
+    sub_rp = np.zeros(rows.shape[0] + 1, dtype=np.int64)
+    np.cumsum(lens, out=sub_rp[1:])
+    total = int(sub_rp[-1])
+    idx = np.arange(total, dtype=np.int64) - np.repeat(sub_rp[:-1], lens) + np.repeat(starts, lens)
+    return (
+        sub_rp.astype(np.int32),
+        np.ascontiguousarray(A.col_idx[idx], dtype=np.int32),
+        np.ascontiguousarray(A.val[idx], dtype=np.float64),
+    )
+
+
+def gspmv_csr(view, X: np.ndarray) -> np.ndarray:
+    """Y = A_sub X for a row subset (from rows_view) of a matrix whose columns index X's rows."""
+    sub_rp, sub_col, sub_val = view
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    m = X.shape[1]
+    nrows = sub_rp.shape[0] - 1
+    Y = np.empty((nrows, m), dtype=np.float64)
+    lib().oracle_gspmv(nrows, _p(sub_rp), _p(sub_col), _p(sub_val), m, _p(X), _p(Y))
+    return Y
+
+
+def gspmv_rows(A, rows, X: np.ndarray) -> np.ndarray:
+    """Rows ``rows`` of Y = A X by the definition of Section 2.3, for sampled checks at full size."""
+    return gspmv_csr(rows_view(A, rows), X)

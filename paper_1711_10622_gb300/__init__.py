@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) hot path of the multiple-ensemble method of arXiv 1711.10622.
+
+m pressure-Poisson solves that share one sparse matrix: the generalised SpMV Y = A X on an
+n x m row-interleaved block, inside a multi-RHS BiCGStab with block vector updates, per-column
+dot products and a Chebyshev polynomial preconditioner. The computation lives in the C-ABI
+library libensemble_solve.so (include/ensemble_solve.h); this package is its Python binding.
+"""
+
+from .api import Matrix, EnsError, gspmv, gspmv_host, version  # noqa: F401
+
+__all__ = ["Matrix", "EnsError", "gspmv", "gspmv_host", "version"]

@@ -1,0 +1,81 @@
+"""ctypes loader for libensemble_solve.so (the C ABI declared in include/ensemble_solve.h).
+
+The library must have been built (``python -m paper_1711_10622_gb300.build`` or
+``__graft_entry__.build()``); there is no fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+ENS_OK, ENS_ERR_INVALID, ENS_ERR_OOM, ENS_ERR_CUDA, ENS_ERR_TIMEOUT, ENS_ERR_BUDGET, ENS_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {
+    0: "ENS_OK",
+    1: "ENS_ERR_INVALID",
+    2: "ENS_ERR_OOM",
+    3: "ENS_ERR_CUDA",
+    4: "ENS_ERR_TIMEOUT",
+    5: "ENS_ERR_BUDGET",
+    6: "ENS_ERR_UNSUPPORTED",
+}
+ENS_F64, ENS_F32 = 0, 1
+ENS_MATRIX_SINGULAR = 0x1
+ENS_F64_AUTO, ENS_F64_NATIVE, ENS_F64_SPLIT = 0, 1, 2
+COL_CONVERGED, COL_MAXITER, COL_BREAKDOWN, COL_NONFINITE, COL_INCOMPATIBLE = range(5)
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+
+
+class EnsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libensemble_solve.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with `python -m paper_1711_10622_gb300.build` "
+            "(there is no CPU fallback for the ensemble solver)"
+        )
+    L = ctypes.CDLL(path)
+    sig = {
+        "ens_create_matrix": (_i32, [_i64, _i64, _vp, _vp, _vp, _u32, _vp, ctypes.POINTER(_vp)]),
+        "ens_destroy_matrix": (_i32, [_vp]),
+        "ens_matrix_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
+        "ens_set_f64_mode": (_i32, [_vp, _i32]),
+        "ens_gspmv": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+        "ens_gspmv_host": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+        "ens_last_error": (ctypes.c_char_p, []),
+        "ens_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != ENS_OK:
+        msg = lib().ens_last_error().decode(errors="replace")
+        raise EnsError(status, msg)

@@ -1,0 +1,150 @@
+"""Python binding of the ensemble-solve C ABI: argument marshalling only.
+
+Tensors are PyTorch CUDA tensors (device memory and streams come from PyTorch); every step of
+the computation runs in libensemble_solve.so. Blocks are (n, m) C-contiguous tensors, i.e. the
+row-interleaved layout of Section 2.3 (element (k, l) at k*m + l).
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+from ._native import EnsError  # noqa: F401
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float64:
+        return N.ENS_F64
+    if t.dtype == torch.float32:
+        return N.ENS_F32
+    raise TypeError(f"unsupported dtype {t.dtype}; expected float64 or float32")
+
+
+def _np_dtype_code(a: np.ndarray):
+    if a.dtype == np.float64:
+        return N.ENS_F64
+    if a.dtype == np.float32:
+        return N.ENS_F32
+    raise TypeError(f"unsupported dtype {a.dtype}")
+
+
+class Matrix:
+    """A device-resident CSR matrix owned by the library (ens_create_matrix)."""
+
+    def __init__(self, row_ptr, col_idx, val, singular: bool = False, stream=None):
+        L = N.lib()
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        n = row_ptr.shape[0] - 1
+        h = ctypes.c_void_p()
+        st = L.ens_create_matrix(
+            n,
+            col_idx.shape[0],
+            row_ptr.ctypes.data_as(ctypes.c_void_p),
+            col_idx.ctypes.data_as(ctypes.c_void_p),
+            val.ctypes.data_as(ctypes.c_void_p),
+            N.ENS_MATRIX_SINGULAR if singular else 0,
+            _stream_handle(stream),
+            ctypes.byref(h),
+        )
+        N.check(st)
+        self._h = h
+        self.singular = bool(singular)
+        n_, nnz_, mr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        N.check(L.ens_matrix_info(self._h, ctypes.byref(n_), ctypes.byref(nnz_), ctypes.byref(mr)))
+        self.n, self.nnz, self.max_row_len = n_.value, nnz_.value, mr.value
+
+    @classmethod
+    def from_operator(cls, op, stream=None):
+        return cls(op.row_ptr, op.col_idx, op.val, singular=op.singular, stream=stream)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("matrix has been destroyed")
+        return self._h
+
+    def set_f64_mode(self, mode: str):
+        code = {"auto": N.ENS_F64_AUTO, "native": N.ENS_F64_NATIVE, "split": N.ENS_F64_SPLIT}[mode]
+        N.check(N.lib().ens_set_f64_mode(self.handle, code))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            N.check(N.lib().ens_destroy_matrix(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _check_block(A: Matrix, t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() != 2 or t.shape[0] != A.n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous ({A.n}, m) tensor, got {tuple(t.shape)}")
+
+
+def gspmv(A: Matrix, X, Y=None, stream=None):
+    """Y = A X (ens_gspmv); X, Y are (n, m) float64 or float32 CUDA tensors."""
+    import torch
+
+    _check_block(A, X, "X")
+    if Y is None:
+        Y = torch.empty_like(X)
+    _check_block(A, Y, "Y")
+    if Y.dtype != X.dtype or Y.shape != X.shape:
+        raise ValueError("X and Y must have the same shape and dtype")
+    N.check(
+        N.lib().ens_gspmv(
+            A.handle, X.shape[1], _dtype_code(X), ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), _stream_handle(stream)
+        )
+    )
+    return Y
+
+
+def gspmv_host(A: Matrix, X: np.ndarray, Y: np.ndarray | None = None, stream=None) -> np.ndarray:
+    """Y = A X with host arrays (ens_gspmv_host; copies inside, synchronous)."""
+    if X.ndim != 2 or X.shape[0] != A.n or not X.flags.c_contiguous:
+        raise ValueError(f"X must be a C-contiguous ({A.n}, m) array")
+    if Y is None:
+        Y = np.empty_like(X)
+    if Y.shape != X.shape or Y.dtype != X.dtype or not Y.flags.c_contiguous:
+        raise ValueError("Y must match X")
+    N.check(
+        N.lib().ens_gspmv_host(
+            A.handle,
+            X.shape[1],
+            _np_dtype_code(X),
+            X.ctypes.data_as(ctypes.c_void_p),
+            Y.ctypes.data_as(ctypes.c_void_p),
+            _stream_handle(stream),
+        )
+    )
+    return Y
+
+
+def version() -> str:
+    return N.lib().ens_version().decode()

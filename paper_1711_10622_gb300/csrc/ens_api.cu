@@ -1,0 +1,238 @@
+// C ABI of libensemble_solve.so: matrix lifetime, GSpMV entry points and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ens_internal.cuh"
+
+namespace ens {
+
+static thread_local std::string g_last_error;
+
+ens_status fail(ens_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+ens_status cuda_fail(cudaError_t e, const char *what) {
+  const ens_status st = (e == cudaErrorMemoryAllocation) ? ENS_ERR_OOM : ENS_ERR_CUDA;
+  return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+namespace {
+
+// Per-row set-up: inverse diagonal (Jacobi scaling) and the float32 / split copies of val.
+// flags[0] |= 1 if some nonzero value lies outside the split product range,
+// flags[0] |= 2 if some row has no nonzero diagonal entry.
+__global__ void k_matrix_aux(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ va, float *__restrict__ v32, float2 *__restrict__ vs,
+                             double *__restrict__ dinv, float *__restrict__ dinv32, unsigned *flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned local = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double d = 0.0;
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j) {
+      const double v = va[j];
+      if (ci[j] == i) d = v;
+      v32[j] = (float)v;
+      const float hi = (float)v;
+      const float lo = (float)(v - (double)hi);
+      vs[j] = make_float2(hi, lo);
+      const double a = fabs(v);
+      // split range of the product path: 2^-50 <= |v| < 2^61, or v == 0
+      if (v != 0.0 && !(a >= 0x1p-50 && a < 0x1p61)) local |= 1u;
+    }
+    if (d == 0.0) local |= 2u;
+    dinv[i] = d != 0.0 ? 1.0 / d : 0.0;
+    dinv32[i] = d != 0.0 ? (float)(1.0 / d) : 0.f;
+  }
+  if (local) atomicOr(flags, local);
+}
+
+template <typename T>
+cudaError_t dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+void free_matrix(ens_matrix *A) {
+  cudaFree(A->row);
+  cudaFree(A->col);
+  cudaFree(A->val);
+  cudaFree(A->val32);
+  cudaFree(A->valsplit);
+  cudaFree(A->dinv);
+  cudaFree(A->dinv32);
+  cudaFree(A->stage_x);
+  cudaFree(A->stage_y);
+  cudaFree(A->ws);
+  delete A;
+}
+
+ens_status check_gspmv_args(const ens_matrix *A, int32_t m, int32_t dtype, const void *X, const void *Y) {
+  if (!A) return fail(ENS_ERR_INVALID, "gspmv: matrix is NULL");
+  if (m < 1) return fail(ENS_ERR_INVALID, "gspmv: m must be >= 1 (got %d)", m);
+  if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "gspmv: unknown dtype %d", dtype);
+  if ((int64_t)m * A->n > ((int64_t)1 << 62) / 8) return fail(ENS_ERR_INVALID, "gspmv: n*m too large");
+  if (A->n > 0 && (!X || !Y)) return fail(ENS_ERR_INVALID, "gspmv: X or Y is NULL");
+  const size_t es = dtype == ENS_F64 ? 8 : 4;
+  if ((uintptr_t)X % es || (uintptr_t)Y % es) return fail(ENS_ERR_INVALID, "gspmv: X/Y not aligned to the element size");
+  const size_t bytes = (size_t)A->n * m * es;
+  const char *x = (const char *)X, *y = (const char *)Y;
+  if (A->n > 0 && x < y + bytes && y < x + bytes) return fail(ENS_ERR_INVALID, "gspmv: X and Y overlap");
+  return ENS_OK;
+}
+
+}  // namespace
+}  // namespace ens
+
+using namespace ens;
+
+extern "C" {
+
+const char *ens_last_error(void) { return g_last_error.c_str(); }
+
+const char *ens_version(void) { return "ensemble_solve 0.1 (sm_103a)"; }
+
+ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                             const double *val, uint32_t flags, void *stream, ens_matrix **out) {
+  clear_error();
+  if (!out) return fail(ENS_ERR_INVALID, "create_matrix: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > INT32_MAX) return fail(ENS_ERR_INVALID, "create_matrix: n = %lld outside [1, 2^31-1]", (long long)n);
+  if (nnz < 0 || nnz > INT32_MAX) return fail(ENS_ERR_INVALID, "create_matrix: nnz = %lld outside [0, 2^31-1]", (long long)nnz);
+  if (!row_ptr || (nnz > 0 && (!col_idx || !val))) return fail(ENS_ERR_INVALID, "create_matrix: NULL array");
+  if (flags & ~ENS_MATRIX_SINGULAR) return fail(ENS_ERR_INVALID, "create_matrix: unknown flags 0x%x", flags);
+  // Host-side validation of the CSR structure.
+  if (row_ptr[0] != 0) return fail(ENS_ERR_INVALID, "create_matrix: row_ptr[0] = %d, expected 0", row_ptr[0]);
+  int32_t max_len = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t len = row_ptr[i + 1] - row_ptr[i];
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(ENS_ERR_INVALID, "create_matrix: row_ptr decreases at row %lld", (long long)i);
+    if (len > max_len) max_len = len;
+  }
+  if (row_ptr[n] != nnz) return fail(ENS_ERR_INVALID, "create_matrix: row_ptr[n] = %d != nnz = %lld", row_ptr[n], (long long)nnz);
+  for (int64_t j = 0; j < nnz; ++j)
+    if (col_idx[j] < 0 || col_idx[j] >= n)
+      return fail(ENS_ERR_INVALID, "create_matrix: col_idx[%lld] = %d outside [0, n)", (long long)j, col_idx[j]);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  ens_matrix *A = new ens_matrix();
+  A->n = n;
+  A->nnz = nnz;
+  A->max_row_len = max_len;
+  A->flags = flags;
+  cudaError_t e = cudaGetDevice(&A->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&A->num_sms, cudaDevAttrMultiProcessorCount, A->device);
+  unsigned *dflags = nullptr;
+  if (e == cudaSuccess) e = dmalloc(&A->row, n + 1);
+  if (e == cudaSuccess) e = dmalloc(&A->col, nnz);
+  if (e == cudaSuccess) e = dmalloc(&A->val, nnz);
+  if (e == cudaSuccess) e = dmalloc(&A->val32, nnz);
+  if (e == cudaSuccess) e = dmalloc(&A->valsplit, nnz);
+  if (e == cudaSuccess) e = dmalloc(&A->dinv, n);
+  if (e == cudaSuccess) e = dmalloc(&A->dinv32, n);
+  if (e == cudaSuccess) e = dmalloc(&dflags, 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A->row, row_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->col, col_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->val, val, nnz * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dflags, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)A->num_sms * 8);
+    k_matrix_aux<<<grid, 256, 0, s>>>((int32_t)n, A->row, A->col, A->val, A->val32, A->valsplit, A->dinv, A->dinv32, dflags);
+    e = cudaGetLastError();
+  }
+  unsigned hflags = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, dflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dflags);
+  if (e != cudaSuccess) {
+    free_matrix(A);
+    return cuda_fail(e, "create_matrix");
+  }
+  A->split_ok = (hflags & 1u) == 0;
+  A->full_diag = (hflags & 2u) == 0;
+  *out = A;
+  return ENS_OK;
+}
+
+ens_status ens_destroy_matrix(ens_matrix *A) {
+  clear_error();
+  if (!A) return ENS_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_matrix(A);
+  if (e != cudaSuccess) return cuda_fail(e, "destroy_matrix");
+  return ENS_OK;
+}
+
+ens_status ens_matrix_info(const ens_matrix *A, int64_t *n, int64_t *nnz, int32_t *max_row_len) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "matrix_info: matrix is NULL");
+  if (n) *n = A->n;
+  if (nnz) *nnz = A->nnz;
+  if (max_row_len) *max_row_len = A->max_row_len;
+  return ENS_OK;
+}
+
+ens_status ens_set_f64_mode(ens_matrix *A, int32_t mode) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "set_f64_mode: matrix is NULL");
+  if (mode < ENS_F64_AUTO || mode > ENS_F64_SPLIT) return fail(ENS_ERR_INVALID, "set_f64_mode: unknown mode %d", mode);
+  A->f64_mode = mode;
+  return ENS_OK;
+}
+
+ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream) {
+  clear_error();
+  ens_status st = check_gspmv_args(A, m, dtype, X, Y);
+  if (st != ENS_OK) return st;
+  return launch_gspmv(A, m, dtype, X, Y, (cudaStream_t)stream);
+}
+
+ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "gspmv_host: matrix is NULL");
+  if (m < 1) return fail(ENS_ERR_INVALID, "gspmv_host: m must be >= 1 (got %d)", m);
+  if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "gspmv_host: unknown dtype %d", dtype);
+  if (!X || !Y) return fail(ENS_ERR_INVALID, "gspmv_host: X or Y is NULL");
+  const size_t bytes = (size_t)A->n * m * (dtype == ENS_F64 ? 8 : 4);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (bytes > A->stage_bytes) {
+    ENS_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(A->stage_x);
+    cudaFree(A->stage_y);
+    A->stage_x = A->stage_y = nullptr;
+    A->stage_bytes = 0;
+    ENS_CUDA_TRY(cudaMalloc(&A->stage_x, bytes));
+    cudaError_t e = cudaMalloc(&A->stage_y, bytes);
+    if (e != cudaSuccess) {
+      cudaFree(A->stage_x);
+      A->stage_x = nullptr;
+      return cuda_fail(e, "gspmv_host staging");
+    }
+    A->stage_bytes = bytes;
+  }
+  ENS_CUDA_TRY(cudaMemcpyAsync(A->stage_x, X, bytes, cudaMemcpyHostToDevice, s));
+  ens_status st = launch_gspmv(A, m, dtype, A->stage_x, A->stage_y, s);
+  if (st != ENS_OK) return st;
+  ENS_CUDA_TRY(cudaMemcpyAsync(Y, A->stage_y, bytes, cudaMemcpyDeviceToHost, s));
+  ENS_CUDA_TRY(cudaStreamSynchronize(s));
+  return ENS_OK;
+}
+
+}  // extern "C"

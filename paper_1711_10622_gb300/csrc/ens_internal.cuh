@@ -1,0 +1,55 @@
+// Internal declarations shared by the translation units of libensemble_solve.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "ensemble_solve.h"
+
+struct ens_matrix {
+  int64_t n = 0, nnz = 0;
+  int32_t max_row_len = 0;
+  uint32_t flags = 0;
+  int device = 0;
+  int num_sms = 0;
+  int32_t *row = nullptr;     // [n+1]
+  int32_t *col = nullptr;     // [nnz]
+  double *val = nullptr;      // [nnz]
+  float *val32 = nullptr;     // [nnz] float32 copy of val (round to nearest)
+  float2 *valsplit = nullptr; // [nnz] (hi, lo): hi = fl32(v), lo = fl32(v - hi)
+  double *dinv = nullptr;     // [n] 1 / A[i,i] (0 where the diagonal is missing or zero)
+  float *dinv32 = nullptr;    // [n]
+  bool split_ok = false;      // every value lies in the split-float product range
+  bool full_diag = false;     // every row has a nonzero diagonal entry
+  int32_t f64_mode = ENS_F64_AUTO;
+  // staging buffers of ens_gspmv_host (grown on demand)
+  void *stage_x = nullptr, *stage_y = nullptr;
+  size_t stage_bytes = 0;
+  // solver workspace (grown on demand)
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace ens {
+
+// Record a formatted message for ens_last_error() and return `st`.
+ens_status fail(ens_status st, const char *fmt, ...);
+// Record a CUDA failure (message includes cudaGetErrorString) and return ENS_ERR_CUDA/OOM.
+ens_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+// Enqueue Y = A X; arguments already validated.
+ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s);
+
+// Launch configuration shared by the streaming kernels: 256 threads, grid-stride.
+constexpr int kThreads = 256;
+
+}  // namespace ens
+
+#define ENS_CUDA_TRY(call)                                   \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return ens::cuda_fail(_e, #call); \
+  } while (0)
