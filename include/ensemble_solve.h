@@ -102,6 +102,57 @@ ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *
  */
 ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream);
 
+/* ---------------------------------------------------------------- multi-RHS BiCGStab solve */
+
+typedef enum { ENS_PRECOND_NONE = 0, ENS_PRECOND_CHEBYSHEV = 1 } ens_precond;
+typedef enum { ENS_PREC_F64 = 0, ENS_PREC_MIXED = 1 } ens_precision;
+
+typedef struct {
+  int32_t max_iter;    /* BiCGStab iterations per column (per inner solve in mixed mode); default 10000 */
+  int32_t precond;     /* ENS_PRECOND_NONE (default) or ENS_PRECOND_CHEBYSHEV */
+  int32_t cheb_steps;  /* Chebyshev updates per application, >= 1 (default 4 = 3 GSpMVs; polynomial
+                          of degree cheb_steps - 1 in D^-1 A) */
+  double cheb_lo;      /* eigenvalue interval [cheb_lo, cheb_hi] of D^-1 A, 0 < lo < hi */
+  double cheb_hi;      /* (default [2/30, 2]; 2 bounds D^-1 A of diagonally dominant M-matrices) */
+  int32_t precision;   /* ENS_PREC_F64 (default) or ENS_PREC_MIXED: FP32 inner BiCGStab with FP32
+                          reductions, FP64 outer residual r = b - A x and correction x += d */
+  double inner_tol;    /* mixed: relative residual of each FP32 inner solve (default 1e-4) */
+  int32_t max_outer;   /* mixed: refinement steps (default 30) */
+  int32_t check_every; /* iterations between host reads of the convergence flags (default 1) */
+  int32_t x0_zero;     /* nonzero: ignore X on input and start from x0 = 0 */
+} ens_solve_opts;
+
+/* Host arrays of m entries each, filled on return; any pointer may be NULL. */
+typedef struct {
+  int32_t *iters;  /* BiCGStab iterations (summed over the inner solves in mixed mode) */
+  double *relres;  /* true relative residual ||b - A x||_2 / ||b||_2 at exit (0 if b = 0, NaN for
+                      NONFINITE / INCOMPATIBLE columns rejected before iterating) */
+  int32_t *status; /* ens_col_status */
+  int32_t *outer;  /* refinement steps (mixed mode), 0 otherwise */
+} ens_solve_stats;
+
+/* Fill *o with the defaults listed above. */
+void ens_default_solve_opts(ens_solve_opts *o);
+
+/*
+ * Solve A x_l = b_l for the m columns of B at once (Section 2.2: the m pressure solves of the
+ * ensemble share the matrix, only the right-hand sides differ; Section 4.1: BiCGStab). Each
+ * column runs its own BiCGStab recurrence (van der Vorst 1992; right preconditioning, per-column
+ * alpha, beta, omega, rho) and every iteration shares one GSpMV over the whole block; converged
+ * columns are frozen. Stops column l when ||b_l - A x_l||_2 / ||b_l||_2 <= tol[l] (the recursive
+ * residual, checked after each half step), then reports the true residual.
+ *   B    DEVICE, n x m row-interleaved float64 (read)
+ *   X    DEVICE, n x m row-interleaved float64: initial guess in (unless opts->x0_zero), solution out
+ *   tol  HOST, m finite values >= 0
+ *   opts may be NULL (defaults); stats may be NULL.
+ * With ENS_MATRIX_SINGULAR the operator's null space is the constants: a column whose sum exceeds
+ * 1e-10 sqrt(n) ||b_l|| is rejected (ENS_COL_INCOMPATIBLE) and every solution is returned with
+ * zero mean. Supports 1 <= m <= 64. Synchronous: returns when X and stats are written.
+ * Workspace (about 8-13 n x m blocks) is allocated stream-ordered for the call and released.
+ */
+ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
+                           const ens_solve_opts *opts, ens_solve_stats *stats, void *stream);
+
 /* Human-readable message of the last failed call on this host thread ("" if none). */
 const char *ens_last_error(void);
 

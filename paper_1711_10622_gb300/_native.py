@@ -32,6 +32,38 @@ _i64 = ctypes.c_int64
 _u32 = ctypes.c_uint32
 
 
+ENS_PRECOND_NONE, ENS_PRECOND_CHEBYSHEV = 0, 1
+ENS_PREC_F64, ENS_PREC_MIXED = 0, 1
+
+
+class SolveOpts(ctypes.Structure):
+    """Mirror of ens_solve_opts (include/ensemble_solve.h)."""
+
+    _fields_ = [
+        ("max_iter", ctypes.c_int32),
+        ("precond", ctypes.c_int32),
+        ("cheb_steps", ctypes.c_int32),
+        ("cheb_lo", ctypes.c_double),
+        ("cheb_hi", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("inner_tol", ctypes.c_double),
+        ("max_outer", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+        ("x0_zero", ctypes.c_int32),
+    ]
+
+
+class SolveStats(ctypes.Structure):
+    """Mirror of ens_solve_stats."""
+
+    _fields_ = [
+        ("iters", ctypes.c_void_p),
+        ("relres", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+        ("outer", ctypes.c_void_p),
+    ]
+
+
 class EnsError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -64,6 +96,11 @@ def lib():
         "ens_set_f64_mode": (_i32, [_vp, _i32]),
         "ens_gspmv": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_gspmv_host": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+        "ens_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),
+        "ens_solve_block": (
+            _i32,
+            [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp],
+        ),
         "ens_last_error": (ctypes.c_char_p, []),
         "ens_version": (ctypes.c_char_p, []),
     }

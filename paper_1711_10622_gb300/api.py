@@ -146,5 +146,71 @@ def gspmv_host(A: Matrix, X: np.ndarray, Y: np.ndarray | None = None, stream=Non
     return Y
 
 
+COL_STATUS = {0: "converged", 1: "maxiter", 2: "breakdown", 3: "nonfinite", 4: "incompatible"}
+
+
+def solve_opts(**kw) -> N.SolveOpts:
+    """ens_solve_opts with the library defaults, overridden by keyword (precond / precision may be
+    given by name: 'none' | 'chebyshev', 'f64' | 'mixed')."""
+    o = N.SolveOpts()
+    N.lib().ens_default_solve_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "precond":
+            v = {"none": N.ENS_PRECOND_NONE, "chebyshev": N.ENS_PRECOND_CHEBYSHEV}.get(v, v)
+        if k == "precision":
+            v = {"f64": N.ENS_PREC_F64, "mixed": N.ENS_PREC_MIXED}.get(v, v)
+        if k == "x0_zero":
+            v = int(bool(v))
+        setattr(o, k, v)
+    return o
+
+
+def solve_block(A: Matrix, B, X=None, tol=1e-8, stream=None, **opts):
+    """Solve A X = B for all m columns (ens_solve_block). B: (n, m) float64 CUDA tensor; X (same
+    shape) holds the initial guess unless omitted (then x0 = 0) and receives the solution.
+
+    Returns (X, stats) with stats = dict(iters, relres, status, outer) as numpy arrays.
+    """
+    import torch
+
+    _check_block(A, B, "B")
+    if B.dtype != torch.float64:
+        raise TypeError("B must be float64")
+    m = B.shape[1]
+    if X is None:
+        X = torch.zeros_like(B)
+        opts.setdefault("x0_zero", True)
+    _check_block(A, X, "X")
+    if X.dtype != torch.float64 or X.shape != B.shape:
+        raise ValueError("X must be a float64 tensor shaped like B")
+    tolv = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), (m,)))
+    iters = np.zeros(m, dtype=np.int32)
+    relres = np.zeros(m, dtype=np.float64)
+    status = np.zeros(m, dtype=np.int32)
+    outer = np.zeros(m, dtype=np.int32)
+    st = N.SolveStats(
+        iters.ctypes.data_as(ctypes.c_void_p),
+        relres.ctypes.data_as(ctypes.c_void_p),
+        status.ctypes.data_as(ctypes.c_void_p),
+        outer.ctypes.data_as(ctypes.c_void_p),
+    )
+    o = solve_opts(**opts)
+    N.check(
+        N.lib().ens_solve_block(
+            A.handle,
+            m,
+            ctypes.c_void_p(B.data_ptr()),
+            ctypes.c_void_p(X.data_ptr()),
+            tolv.ctypes.data_as(ctypes.c_void_p),
+            ctypes.byref(o),
+            ctypes.byref(st),
+            _stream_handle(stream),
+        )
+    )
+    return X, {"iters": iters, "relres": relres, "status": status, "outer": outer}
+
+
 def version() -> str:
     return N.lib().ens_version().decode()

@@ -53,8 +53,8 @@ __global__ void k_matrix_aux(int32_t n, const int32_t *__restrict__ rp, const in
       const float lo = (float)(v - (double)hi);
       vs[j] = make_float2(hi, lo);
       const double a = fabs(v);
-      // split range of the product path: 2^-50 <= |v| < 2^61, or v == 0
-      if (v != 0.0 && !(a >= 0x1p-50 && a < 0x1p61)) local |= 1u;
+      // split range of the product path: 2^-40 <= |v| < 2^60, or v == 0
+      if (v != 0.0 && !(a >= 0x1p-40 && a < 0x1p60)) local |= 1u;
     }
     if (d == 0.0) local |= 2u;
     dinv[i] = d != 0.0 ? 1.0 / d : 0.0;

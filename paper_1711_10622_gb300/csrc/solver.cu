@@ -1,0 +1,84 @@
+// C ABI of the multi-RHS solve: option defaults, validation and dispatch on the FP64 arithmetic.
+// The solver itself is in solver_impl.cuh (instantiated in solver_{f32,split,native}.cu).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "ens_internal.cuh"
+#include "reduce.cuh"
+
+namespace ens {
+
+bool use_split(const ens_matrix *A);
+
+namespace solver {
+ens_status solve_f64_split(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                           const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s);
+ens_status solve_f64_native(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                            const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s);
+}  // namespace solver
+
+namespace {
+
+ens_status validate_solve(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
+                          const ens_solve_opts &o) {
+  if (!A) return fail(ENS_ERR_INVALID, "solve_block: matrix is NULL");
+  if (m < 1 || m > kMaxSolveM) return fail(ENS_ERR_INVALID, "solve_block: m = %d outside [1, %d]", m, kMaxSolveM);
+  if (!B || !X) return fail(ENS_ERR_INVALID, "solve_block: B or X is NULL");
+  if (!tol) return fail(ENS_ERR_INVALID, "solve_block: tol is NULL");
+  for (int l = 0; l < m; ++l)
+    if (!(tol[l] >= 0.0) || !std::isfinite(tol[l]))
+      return fail(ENS_ERR_INVALID, "solve_block: tol[%d] must be finite and >= 0", l);
+  if ((uintptr_t)B % 8 || (uintptr_t)X % 8) return fail(ENS_ERR_INVALID, "solve_block: B/X not 8-byte aligned");
+  if (o.max_iter < 0) return fail(ENS_ERR_INVALID, "solve_block: max_iter < 0");
+  if (o.precond != ENS_PRECOND_NONE && o.precond != ENS_PRECOND_CHEBYSHEV)
+    return fail(ENS_ERR_INVALID, "solve_block: unknown preconditioner %d", o.precond);
+  if (o.precond == ENS_PRECOND_CHEBYSHEV) {
+    if (o.cheb_steps < 1 || o.cheb_steps > 64) return fail(ENS_ERR_INVALID, "solve_block: cheb_steps outside [1, 64]");
+    if (!(o.cheb_lo > 0.0) || !(o.cheb_hi > o.cheb_lo) || !std::isfinite(o.cheb_hi))
+      return fail(ENS_ERR_INVALID, "solve_block: need 0 < cheb_lo < cheb_hi");
+    if (!A->full_diag) return fail(ENS_ERR_INVALID, "solve_block: Chebyshev needs a nonzero diagonal in every row");
+  }
+  if (o.precision != ENS_PREC_F64 && o.precision != ENS_PREC_MIXED)
+    return fail(ENS_ERR_INVALID, "solve_block: unknown precision %d", o.precision);
+  if (o.precision == ENS_PREC_MIXED && (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0) || o.max_outer < 1))
+    return fail(ENS_ERR_INVALID, "solve_block: mixed mode needs 0 < inner_tol < 1 and max_outer >= 1");
+  if (o.check_every < 1) return fail(ENS_ERR_INVALID, "solve_block: check_every < 1");
+  return ENS_OK;
+}
+
+}  // namespace
+}  // namespace ens
+
+using namespace ens;
+extern "C" {
+
+void ens_default_solve_opts(ens_solve_opts *o) {
+  if (!o) return;
+  o->max_iter = 10000;
+  o->precond = ENS_PRECOND_NONE;
+  o->cheb_steps = 4;
+  o->cheb_lo = 2.0 / 30.0;
+  o->cheb_hi = 2.0;
+  o->precision = ENS_PREC_F64;
+  o->inner_tol = 1e-4;
+  o->max_outer = 30;
+  o->check_every = 1;
+  o->x0_zero = 0;
+}
+
+ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
+                           const ens_solve_opts *opts, ens_solve_stats *stats, void *stream) {
+  clear_error();
+  ens_solve_opts o;
+  ens_default_solve_opts(&o);
+  if (opts) o = *opts;
+  ens_status st = validate_solve(A, m, B, X, tol, o);
+  if (st != ENS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (use_split(A)) return solver::solve_f64_split(A, m, B, X, tol, o, stats, s);
+  return solver::solve_f64_native(A, m, B, X, tol, o, stats, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,878 @@
+// Multi-RHS BiCGStab on an n x m row-interleaved block (Sections 2.2 and 4.1), with an optional
+// Jacobi-scaled Chebyshev polynomial preconditioner and an FP32-inner / FP64-outer
+// mixed-precision mode.
+//
+// The m right-hand sides run m independent BiCGStab recurrences (per-column rho, alpha, omega,
+// beta); every operator application is one GSpMV over the whole block, so the matrix is read
+// once per product for all m columns. Per iteration (right preconditioning, M^-1 = Chebyshev
+// polynomial or identity):
+//   k_p     p = r + beta (p - omega v)            [+ d0 = D^-1 p / theta, ph = d0]
+//   k_cheb  (cheb_steps - 1) x: GSpMV of d, fused 3-term update of d, z = ph, residual
+//   k_v     v = A ph,  (rhat, v)  -> alpha       (dot fused into the GSpMV epilogue)
+//   k_s     s = r - alpha v,  ||s||^2 -> half-step convergence   [+ Chebyshev start for s]
+//   k_cheb  ... z = sh
+//   k_t     t = A sh, (t, s), (t, t) -> omega     (dots fused into the GSpMV epilogue)
+//   k_xr    x += alpha ph + omega sh, r = s - omega t, ||r||^2, (rhat, r) -> convergence, rho
+// The per-column scalar step runs in the last block of each reduction (reduce.cuh), so the
+// scalars never leave the device; the host only reads the m convergence flags every
+// check_every iterations. Converged columns are frozen (their x is no longer updated).
+//
+// The solver works on internal copies of B and X whose row stride is m rounded up to an even
+// width, so every kernel uses 16-byte row-segment accesses (m = 1 keeps stride 1).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+#include <vector>
+
+#include "ens_internal.cuh"
+#include "reduce.cuh"
+#include "rowprod.cuh"
+
+namespace ens {
+
+bool use_split(const ens_matrix *A);
+
+namespace solver {
+
+enum : int32_t { ST_ACTIVE = 0, ST_HALF = 1, ST_DONE = 2 };
+enum : int32_t { FL_EARLY = 1, FL_ZERO_B = 2 };
+
+template <typename T>
+struct Cols {
+  T *rho, *rho_old, *alpha, *omega, *bn2, *thr2, *rh2, *rn2, *tol, *mean;
+  int32_t *state, *iters, *status, *flags;
+  double *relres;
+};
+
+template <typename T>
+struct Tiny;
+template <>
+struct Tiny<double> {
+  static constexpr double v = 1e-300;
+};
+template <>
+struct Tiny<float> {
+  static constexpr float v = 1e-30f;
+};
+
+#define ENS_ROWS(i)                                                                           \
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < A.n; \
+       i += (int64_t)gridDim.x * (kThreads / LANES))
+
+// ----------------------------------------------------------------------------- start
+// r = b - A x (or r = b and x = 0 when x0_zero), rhat = r; per column ||b||^2, ||r||^2, sum(b).
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_start(MatView A, int32_t m, const typename Arith::T *__restrict__ b, typename Arith::T *x,
+            typename Arith::T *__restrict__ r, typename Arith::T *__restrict__ rh, int x0_zero, int singular,
+            typename Arith::T incompat, Cols<typename Arith::T> cs, typename Arith::T *partials,
+            unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[3][VEC];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) acc[d][q] = T(0);
+  if (c < m) {
+    ENS_ROWS(i) {
+      T bv[VEC], ax[VEC], rv[VEC];
+      load_vec<T, VEC>(b + i * m + c, bv);
+      if (x0_zero) {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) ax[q] = T(0);
+        store_vec<T, VEC>(x + i * m + c, ax);
+      } else {
+        Arith::template row<VEC>(A, i, m, c, x, ax);
+      }
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        rv[q] = bv[q] - ax[q];
+        acc[0][q] += bv[q] * bv[q];
+        acc[1][q] += rv[q] * rv[q];
+        acc[2][q] += bv[q];
+      }
+      store_vec<T, VEC>(r + i * m + c, rv);
+      if (rh) store_vec<T, VEC>(rh + i * m + c, rv);
+    }
+  }
+  reduce_cols<T, 3, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 3> &t) {
+    const T bn2 = t.v[0][l], rn2 = t.v[1][l], sb = t.v[2][l];
+    const T thr2 = cs.tol[l] * cs.tol[l] * bn2;
+    int32_t st = ST_ACTIVE, status = ENS_COL_CONVERGED, fl = 0;
+    if (!isfinite(bn2) || !isfinite(rn2)) {
+      st = ST_DONE;
+      status = ENS_COL_NONFINITE;
+      fl = FL_EARLY;
+    } else if (bn2 == T(0)) {
+      st = ST_DONE;
+      fl = FL_EARLY | FL_ZERO_B;
+    } else if (singular && fabs(sb) > incompat * sqrt(bn2)) {
+      st = ST_DONE;
+      status = ENS_COL_INCOMPATIBLE;
+      fl = FL_EARLY;
+    } else if (rn2 <= thr2) {
+      st = ST_DONE;
+    }
+    cs.bn2[l] = bn2;
+    cs.thr2[l] = thr2;
+    cs.rn2[l] = rn2;
+    cs.rh2[l] = rn2;
+    cs.rho[l] = rn2;  // rhat = r0, so rho_1 = (rhat, r0) = ||r0||^2
+    cs.rho_old[l] = T(1);
+    cs.alpha[l] = T(1);
+    cs.omega[l] = T(1);
+    cs.state[l] = st;
+    cs.status[l] = status;
+    cs.flags[l] = fl;
+    cs.iters[l] = 0;
+  });
+}
+
+// ----------------------------------------------------------------------------- p update
+// p = r + beta (p - omega v) for active columns; with the preconditioner also the first
+// Chebyshev term d0 = D^-1 p / theta, written to da and to ph (= z).
+template <typename Arith, int VEC, int LANES, bool PREC>
+__global__ void __launch_bounds__(kThreads)
+    k_p(MatView A, int32_t m, const typename Arith::T *__restrict__ r, typename Arith::T *p,
+        const typename Arith::T *__restrict__ v, typename Arith::T *__restrict__ da, typename Arith::T *__restrict__ ph,
+        typename Arith::T inv_theta, Cols<typename Arith::T> cs) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  T beta[VEC], om[VEC];
+  bool act[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    const int l = c + q;
+    act[q] = cs.state[l] == ST_ACTIVE;
+    beta[q] = act[q] ? (cs.rho[l] / cs.rho_old[l]) * (cs.alpha[l] / cs.omega[l]) : T(0);
+    om[q] = act[q] ? cs.omega[l] : T(0);
+  }
+  ENS_ROWS(i) {
+    T rv[VEC], pv[VEC], vv[VEC];
+    load_vec<T, VEC>(r + i * m + c, rv);
+    load_vec_rw<T, VEC>(p + i * m + c, pv);
+    load_vec<T, VEC>(v + i * m + c, vv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) pv[q] = act[q] ? rv[q] + beta[q] * (pv[q] - om[q] * vv[q]) : pv[q];
+    store_vec<T, VEC>(p + i * m + c, pv);
+    if (PREC) {
+      const T sc = Arith::dinv(A, i) * inv_theta;
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) pv[q] *= sc;
+      store_vec<T, VEC>(da + i * m + c, pv);
+      store_vec<T, VEC>(ph + i * m + c, pv);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- Chebyshev step
+// One step k >= 1 of the Chebyshev iteration z = p(D^-1 A) D^-1 src (Saad, Alg. 12.1, Jacobi
+// scaled, zero start), fused with its GSpMV:
+//   res_k = res_{k-1} - A d_{k-1}   (res_0 = src)
+//   d_k   = c1 d_{k-1} + c2 D^-1 res_k,   z += d_k
+// din is the GSpMV input (read by neighbouring rows), so d_k goes to a second buffer. The last
+// step needs neither res_k nor d_k afterwards.
+template <typename Arith, int VEC, int LANES, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kThreads)
+    k_cheb(MatView A, int32_t m, const typename Arith::T *__restrict__ din, typename Arith::T *__restrict__ dout,
+           const typename Arith::T *__restrict__ src, typename Arith::T *res, typename Arith::T *z,
+           typename Arith::T c1, typename Arith::T c2) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  ENS_ROWS(i) {
+    T w[VEC], di[VEC], rs[VEC], zv[VEC], dn[VEC];
+    Arith::template row<VEC>(A, i, m, c, din, w);
+    load_vec<T, VEC>(din + i * m + c, di);
+    if (FIRST)
+      load_vec<T, VEC>(src + i * m + c, rs);
+    else
+      load_vec_rw<T, VEC>(res + i * m + c, rs);
+    load_vec_rw<T, VEC>(z + i * m + c, zv);
+    const T dv = Arith::dinv(A, i);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      rs[q] -= w[q];
+      dn[q] = c1 * di[q] + c2 * (dv * rs[q]);
+      zv[q] += dn[q];
+    }
+    store_vec<T, VEC>(z + i * m + c, zv);
+    if (!LAST) {
+      store_vec<T, VEC>(res + i * m + c, rs);
+      store_vec<T, VEC>(dout + i * m + c, dn);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- v = A ph
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_v(MatView A, int32_t m, const typename Arith::T *__restrict__ ph, typename Arith::T *__restrict__ v,
+        const typename Arith::T *__restrict__ rh, int32_t it, Cols<typename Arith::T> cs,
+        typename Arith::T *partials, unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[1][VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) acc[0][q] = T(0);
+  if (c < m) {
+    ENS_ROWS(i) {
+      T y[VEC], h[VEC];
+      Arith::template row<VEC>(A, i, m, c, ph, y);
+      store_vec<T, VEC>(v + i * m + c, y);
+      load_vec<T, VEC>(rh + i * m + c, h);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[0][q] += h[q] * y[q];
+    }
+  }
+  reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 1> &t) {
+    if (cs.state[l] != ST_ACTIVE) return;
+    cs.iters[l] = it;
+    const T rv = t.v[0][l];
+    if (rv == T(0)) {
+      cs.state[l] = ST_DONE;
+      cs.status[l] = ENS_COL_BREAKDOWN;
+      return;
+    }
+    cs.alpha[l] = cs.rho[l] / rv;
+  });
+}
+
+// ----------------------------------------------------------------------------- s update
+template <typename Arith, int VEC, int LANES, bool PREC>
+__global__ void __launch_bounds__(kThreads)
+    k_s(MatView A, int32_t m, const typename Arith::T *__restrict__ r, const typename Arith::T *__restrict__ v,
+        typename Arith::T *__restrict__ s, typename Arith::T *__restrict__ da, typename Arith::T *__restrict__ sh,
+        typename Arith::T inv_theta, Cols<typename Arith::T> cs, typename Arith::T *partials, unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[1][VEC], al[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    acc[0][q] = T(0);
+    al[q] = (c + q < m && cs.state[c + q] == ST_ACTIVE) ? cs.alpha[c + q] : T(0);
+  }
+  if (c < m) {
+    ENS_ROWS(i) {
+      T rv[VEC], vv[VEC];
+      load_vec<T, VEC>(r + i * m + c, rv);
+      load_vec<T, VEC>(v + i * m + c, vv);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        rv[q] = al[q] != T(0) ? rv[q] - al[q] * vv[q] : rv[q];
+        acc[0][q] += rv[q] * rv[q];
+      }
+      store_vec<T, VEC>(s + i * m + c, rv);
+      if (PREC) {
+        const T sc = Arith::dinv(A, i) * inv_theta;
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) rv[q] *= sc;
+        store_vec<T, VEC>(da + i * m + c, rv);
+        store_vec<T, VEC>(sh + i * m + c, rv);
+      }
+    }
+  }
+  reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 1> &t) {
+    if (cs.state[l] == ST_ACTIVE && t.v[0][l] <= cs.thr2[l]) cs.state[l] = ST_HALF;
+  });
+}
+
+// ----------------------------------------------------------------------------- t = A sh
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_t(MatView A, int32_t m, const typename Arith::T *__restrict__ sh, typename Arith::T *__restrict__ t,
+        const typename Arith::T *__restrict__ s, Cols<typename Arith::T> cs, typename Arith::T *partials,
+        unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[2][VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) acc[0][q] = acc[1][q] = T(0);
+  if (c < m) {
+    ENS_ROWS(i) {
+      T y[VEC], sv[VEC];
+      Arith::template row<VEC>(A, i, m, c, sh, y);
+      store_vec<T, VEC>(t + i * m + c, y);
+      load_vec<T, VEC>(s + i * m + c, sv);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        acc[0][q] += y[q] * sv[q];
+        acc[1][q] += y[q] * y[q];
+      }
+    }
+  }
+  reduce_cols<T, 2, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 2> &tt) {
+    if (cs.state[l] != ST_ACTIVE) return;
+    const T t2 = tt.v[1][l];
+    if (t2 == T(0)) {
+      cs.state[l] = ST_DONE;
+      cs.status[l] = ENS_COL_BREAKDOWN;
+      return;
+    }
+    cs.omega[l] = tt.v[0][l] / t2;
+  });
+}
+
+// ----------------------------------------------------------------------------- x, r update
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_xr(MatView A, int32_t m, typename Arith::T *x, const typename Arith::T *__restrict__ ph,
+         const typename Arith::T *__restrict__ sh, const typename Arith::T *__restrict__ s,
+         const typename Arith::T *__restrict__ t, typename Arith::T *__restrict__ r,
+         const typename Arith::T *__restrict__ rh, int32_t it, int32_t max_iter, Cols<typename Arith::T> cs,
+         typename Arith::T *partials, unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[2][VEC], al[VEC], om[VEC];
+  int st[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    acc[0][q] = acc[1][q] = T(0);
+    st[q] = c + q < m ? cs.state[c + q] : ST_DONE;
+    al[q] = st[q] == ST_DONE ? T(0) : cs.alpha[c + q];
+    om[q] = st[q] == ST_ACTIVE ? cs.omega[c + q] : T(0);
+  }
+  if (c < m) {
+    ENS_ROWS(i) {
+      T xv[VEC], pv[VEC], shv[VEC], sv[VEC], tv[VEC], hv[VEC];
+      load_vec_rw<T, VEC>(x + i * m + c, xv);
+      load_vec<T, VEC>(ph + i * m + c, pv);
+      load_vec<T, VEC>(sh + i * m + c, shv);
+      load_vec<T, VEC>(s + i * m + c, sv);
+      load_vec<T, VEC>(t + i * m + c, tv);
+      load_vec<T, VEC>(rh + i * m + c, hv);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        // frozen columns keep x exactly (no 0 * v products that could turn NaN)
+        const T xa = xv[q] + al[q] * pv[q];
+        xv[q] = st[q] == ST_ACTIVE ? xa + om[q] * shv[q] : st[q] == ST_HALF ? xa : xv[q];
+        sv[q] = st[q] == ST_ACTIVE ? sv[q] - om[q] * tv[q] : sv[q];  // r
+        acc[0][q] += sv[q] * sv[q];
+        acc[1][q] += hv[q] * sv[q];
+      }
+      store_vec<T, VEC>(x + i * m + c, xv);
+      store_vec<T, VEC>(r + i * m + c, sv);
+    }
+  }
+  reduce_cols<T, 2, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 2> &tt) {
+    const int st = cs.state[l];
+    if (st == ST_HALF) {
+      cs.state[l] = ST_DONE;
+      cs.status[l] = ENS_COL_CONVERGED;
+      return;
+    }
+    if (st != ST_ACTIVE) return;
+    const T rn2 = tt.v[0][l], rr = tt.v[1][l];
+    cs.rho_old[l] = cs.rho[l];
+    cs.rn2[l] = rn2;
+    if (!isfinite(rn2)) {
+      cs.state[l] = ST_DONE;
+      cs.status[l] = ENS_COL_NONFINITE;
+    } else if (rn2 <= cs.thr2[l]) {
+      cs.state[l] = ST_DONE;
+      cs.status[l] = ENS_COL_CONVERGED;
+    } else if (cs.omega[l] == T(0)) {
+      cs.state[l] = ST_DONE;
+      cs.status[l] = ENS_COL_BREAKDOWN;
+    } else if (it < max_iter) {  // the next iteration begins: rho and its breakdown test
+      if (!isfinite(rr)) {
+        cs.state[l] = ST_DONE;
+        cs.status[l] = ENS_COL_NONFINITE;
+        cs.iters[l] = it + 1;
+      } else if (fabs(rr) <= Tiny<T>::v * sqrt(cs.rh2[l]) * sqrt(rn2)) {
+        cs.state[l] = ST_DONE;
+        cs.status[l] = ENS_COL_BREAKDOWN;
+        cs.iters[l] = it + 1;
+      } else {
+        cs.rho[l] = rr;
+      }
+    }
+  });
+}
+
+// ----------------------------------------------------------------------------- finishing
+// Column sums of x (singular operators: the solution is normalised to zero mean).
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_colsum(MatView A, int32_t m, const typename Arith::T *__restrict__ x, typename Arith::T inv_n,
+             Cols<typename Arith::T> cs, typename Arith::T *partials, unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[1][VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) acc[0][q] = T(0);
+  if (c < m) {
+    ENS_ROWS(i) {
+      T xv[VEC];
+      load_vec<T, VEC>(x + i * m + c, xv);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[0][q] += xv[q];
+    }
+  }
+  reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter,
+                                [&](int l, const ColTotals<T, 1> &t) { cs.mean[l] = t.v[0][l] * inv_n; });
+}
+
+// x = 0 for zero right-hand sides; x -= mean for singular operators (columns that iterated).
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_fix(MatView A, int32_t m, typename Arith::T *x, int singular, Cols<typename Arith::T> cs) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  bool zero[VEC];
+  T sub[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    const int fl = cs.flags[c + q];
+    zero[q] = (fl & FL_ZERO_B) != 0;
+    sub[q] = (singular && !(fl & FL_EARLY)) ? cs.mean[c + q] : T(0);
+  }
+  ENS_ROWS(i) {
+    T xv[VEC];
+    load_vec_rw<T, VEC>(x + i * m + c, xv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) xv[q] = zero[q] ? T(0) : xv[q] - sub[q];
+    store_vec<T, VEC>(x + i * m + c, xv);
+  }
+}
+
+// True residual ||b - A x||^2 per column -> relres. With `outer` set (mixed mode) the residual is
+// also stored in r and the outer convergence test runs on it.
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ b, const typename Arith::T *__restrict__ x,
+            typename Arith::T *__restrict__ r, int outer, Cols<typename Arith::T> cs, typename Arith::T *partials,
+            unsigned *counter) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  T acc[1][VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) acc[0][q] = T(0);
+  if (c < m) {
+    ENS_ROWS(i) {
+      T y[VEC], bv[VEC];
+      Arith::template row<VEC>(A, i, m, c, x, y);
+      load_vec<T, VEC>(b + i * m + c, bv);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        y[q] = bv[q] - y[q];
+        acc[0][q] += y[q] * y[q];
+      }
+      if (r) store_vec<T, VEC>(r + i * m + c, y);
+    }
+  }
+  reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 1> &t) {
+    const T rr = t.v[0][l];
+    if (outer) {
+      if (cs.state[l] != ST_ACTIVE) return;
+      cs.rn2[l] = rr;
+      if (!isfinite(rr)) {
+        cs.state[l] = ST_DONE;
+        cs.status[l] = ENS_COL_NONFINITE;
+      } else if (rr <= cs.thr2[l]) {
+        cs.state[l] = ST_DONE;
+        cs.status[l] = ENS_COL_CONVERGED;
+      }
+      return;
+    }
+    const int fl = cs.flags[l];
+    cs.relres[l] = (fl & FL_ZERO_B) ? 0.0 : (fl & FL_EARLY) ? (double)NAN : sqrt((double)rr / (double)cs.bn2[l]);
+  });
+}
+
+// ----------------------------------------------------------------------------- mixed precision
+// Inner right-hand side: r32 = r / ||r|| for active outer columns, 0 otherwise (so finished
+// columns start converged in the inner solve).
+template <int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_to32(int32_t n, int32_t m, const double *__restrict__ r, float *__restrict__ r32, Cols<double> cs) {
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  double sc[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) sc[q] = cs.state[c + q] == ST_ACTIVE ? rsqrt(cs.rn2[c + q]) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < n;
+       i += (int64_t)gridDim.x * (kThreads / LANES)) {
+    double rv[VEC];
+    float o[VEC];
+    load_vec<double, VEC>(r + i * m + c, rv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) o[q] = (float)(rv[q] * sc[q]);
+    store_vec<float, VEC>(r32 + i * m + c, o);
+  }
+}
+
+// x += ||r|| d for active outer columns (the FP64 correction step).
+template <int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_correct(int32_t n, int32_t m, double *x, const float *__restrict__ d, Cols<double> cs) {
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  double sc[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) sc[q] = cs.state[c + q] == ST_ACTIVE ? sqrt(cs.rn2[c + q]) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < n;
+       i += (int64_t)gridDim.x * (kThreads / LANES)) {
+    double xv[VEC];
+    float dv[VEC];
+    load_vec_rw<double, VEC>(x + i * m + c, xv);
+    load_vec<float, VEC>(d + i * m + c, dv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) xv[q] += sc[q] * (double)dv[q];
+    store_vec<double, VEC>(x + i * m + c, xv);
+  }
+}
+
+// Copy between the caller's stride-m block and the internal stride-mp block (zero padding).
+static __global__ void k_pad(int64_t n, int32_t m, int32_t mp, const double *__restrict__ src, double *__restrict__ dst) {
+  const int64_t total = n * mp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / mp;
+    const int32_t l = (int32_t)(e - i * mp);
+    dst[e] = l < m ? src[i * m + l] : 0.0;
+  }
+}
+static __global__ void k_unpad(int64_t n, int32_t m, int32_t mp, const double *__restrict__ src, double *__restrict__ dst) {
+  const int64_t total = n * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / m;
+    const int32_t l = (int32_t)(e - i * m);
+    dst[e] = src[i * mp + l];
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+template <typename F>
+cudaError_t with_vl(int vec, int lanes, F &&f) {
+  using std::integral_constant;
+  if (vec == 1) return f(integral_constant<int, 1>{}, integral_constant<int, 1>{});
+  switch (lanes) {
+    case 1: return f(integral_constant<int, 2>{}, integral_constant<int, 1>{});
+    case 2: return f(integral_constant<int, 2>{}, integral_constant<int, 2>{});
+    case 4: return f(integral_constant<int, 2>{}, integral_constant<int, 4>{});
+    case 8: return f(integral_constant<int, 2>{}, integral_constant<int, 8>{});
+    case 16: return f(integral_constant<int, 2>{}, integral_constant<int, 16>{});
+    default: return f(integral_constant<int, 2>{}, integral_constant<int, 32>{});
+  }
+}
+
+// Stream-ordered scratch allocation, released when the object goes out of scope.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void *> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void *p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  cudaError_t get(T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    *p = (T *)q;
+    return cudaSuccess;
+  }
+};
+
+inline MatView view_of(const ens_matrix *A) {
+  return MatView{(int32_t)A->n, A->row, A->col, A->val, A->val32, A->valsplit, A->dinv, A->dinv32};
+}
+
+template <typename T>
+cudaError_t alloc_cols(Scratch &sc, int m, Cols<T> &cs) {
+  cudaError_t e = cudaSuccess;
+  T **tp[] = {&cs.rho, &cs.rho_old, &cs.alpha, &cs.omega, &cs.bn2, &cs.thr2, &cs.rh2, &cs.rn2, &cs.tol, &cs.mean};
+  for (T **p : tp)
+    if (e == cudaSuccess) e = sc.get(p, m);
+  int32_t **ip[] = {&cs.state, &cs.iters, &cs.status, &cs.flags};
+  for (int32_t **p : ip)
+    if (e == cudaSuccess) e = sc.get(p, m);
+  if (e == cudaSuccess) e = sc.get(&cs.relres, m);
+  return e;
+}
+
+// One BiCGStab run over an mp-wide internal block in arithmetic Arith (float64 split/native or
+// float32). b, x are device blocks of stride mp.
+template <typename Arith>
+struct Bicg {
+  using T = typename Arith::T;
+  MatView A;
+  int64_t n = 0;
+  int mp = 0, vec = 2, lanes = 1, grid = 0;
+  bool prec = false;
+  int cheb_steps = 4;
+  double theta = 1, delta = 1;
+  cudaStream_t s = nullptr;
+  T *r, *rh, *p, *v, *ph, *s_, *sh, *t, *da, *db, *res;
+  T *partials;
+  unsigned *counter;
+  Cols<T> cs;
+
+  // outer_only: just the residual block, scalars and reduction scratch (mixed-mode outer loop).
+  cudaError_t setup(Scratch &sc, const ens_matrix *M, int mp_, const ens_solve_opts &o, cudaStream_t st,
+                    bool outer_only = false) {
+    A = view_of(M);
+    n = M->n;
+    mp = mp_;
+    s = st;
+    vec = mp == 1 ? 1 : 2;
+    lanes = 1;
+    while (lanes * vec < mp) lanes <<= 1;
+    grid = M->num_sms * 4;
+    prec = o.precond == ENS_PRECOND_CHEBYSHEV;
+    cheb_steps = o.cheb_steps;
+    theta = 0.5 * (o.cheb_hi + o.cheb_lo);
+    delta = 0.5 * (o.cheb_hi - o.cheb_lo);
+    const size_t blk = (size_t)n * mp;
+    cudaError_t e = cudaSuccess;
+    r = rh = p = v = ph = s_ = sh = t = da = db = res = nullptr;
+    if (outer_only) {
+      prec = false;
+      e = sc.get(&r, blk);
+    } else {
+      T **bufs[] = {&r, &rh, &p, &v, &s_, &t};
+      for (T **b : bufs)
+        if (e == cudaSuccess) e = sc.get(b, blk);
+    }
+    if (outer_only) {
+    } else if (prec) {
+      T **pb[] = {&ph, &sh, &da, &db, &res};
+      for (T **b : pb)
+        if (e == cudaSuccess) e = sc.get(b, blk);
+    } else {
+      ph = p;
+      sh = s_;
+      da = db = res = nullptr;
+    }
+    if (e == cudaSuccess) e = sc.get(&partials, (size_t)grid * 3 * kMaxSolveM);
+    if (e == cudaSuccess) e = sc.get(&counter, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = alloc_cols(sc, mp, cs);
+    return e;
+  }
+
+  cudaError_t start(const T *b, T *x, bool x0_zero, int singular, const std::vector<T> &tol) {
+    cudaError_t e = cudaMemcpyAsync(cs.tol, tol.data(), mp * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (p) e = cudaMemsetAsync(p, 0, (size_t)n * mp * sizeof(T), s);
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, (size_t)n * mp * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+    const T incompat = (T)(1e-10 * std::sqrt((double)n));
+    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+      constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+      k_start<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
+                                                     partials, counter);
+      return cudaGetLastError();
+    });
+  }
+
+  // Chebyshev application z = p(D^-1 A) D^-1 src; the first term is already in da and z.
+  template <int V, int L>
+  void cheb(const T *src, T *z) {
+    const double sigma = theta / delta;
+    double rho_prev = 1.0 / sigma;
+    T *din = da, *dout = db;
+    for (int k = 1; k < cheb_steps; ++k) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta);
+      const bool first = k == 1, last = k == cheb_steps - 1;
+      if (first && last)
+        k_cheb<Arith, V, L, true, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+      else if (first)
+        k_cheb<Arith, V, L, true, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+      else if (last)
+        k_cheb<Arith, V, L, false, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+      else
+        k_cheb<Arith, V, L, false, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+      std::swap(din, dout);
+      rho_prev = rho;
+    }
+  }
+
+  cudaError_t iteration(T *x, int it, int max_iter) {
+    const T inv_theta = (T)(1.0 / theta);
+    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+      constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+      if (prec) {
+        k_p<Arith, V, L, true><<<grid, kThreads, 0, s>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
+        cheb<V, L>(p, ph);
+      } else {
+        k_p<Arith, V, L, false><<<grid, kThreads, 0, s>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
+      }
+      k_v<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, ph, v, rh, it, cs, partials, counter);
+      if (prec) {
+        k_s<Arith, V, L, true><<<grid, kThreads, 0, s>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
+        cheb<V, L>(s_, sh);
+      } else {
+        k_s<Arith, V, L, false><<<grid, kThreads, 0, s>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
+      }
+      k_t<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, sh, t, s_, cs, partials, counter);
+      k_xr<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, ph, sh, s_, t, r, rh, it, max_iter, cs, partials, counter);
+      return cudaGetLastError();
+    });
+  }
+
+  cudaError_t states(std::vector<int32_t> &h) {
+    h.resize(mp);
+    cudaError_t e = cudaMemcpyAsync(h.data(), cs.state, mp * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  }
+
+  static bool all_done(const std::vector<int32_t> &h) {
+    for (int32_t v : h)
+      if (v != ST_DONE) return false;
+    return true;
+  }
+
+  // Iterate until every column is done or max_iter; returns the iterations run.
+  cudaError_t iterate(T *x, int max_iter, int check_every, int *ran) {
+    std::vector<int32_t> h;
+    cudaError_t e = states(h);
+    *ran = 0;
+    if (e != cudaSuccess || all_done(h)) return e;
+    for (int it = 1; it <= max_iter; ++it) {
+      e = iteration(x, it, max_iter);
+      if (e != cudaSuccess) return e;
+      *ran = it;
+      if (it % check_every == 0 || it == max_iter) {
+        e = states(h);
+        if (e != cudaSuccess) return e;
+        if (all_done(h)) break;
+      }
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t finish(const T *b, T *x, int singular) {
+    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+      constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+      if (singular) {
+        k_colsum<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, (T)(1.0 / (double)n), cs, partials, counter);
+      }
+      k_fix<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, singular, cs);
+      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, nullptr, 0, cs, partials, counter);
+      return cudaGetLastError();
+    });
+  }
+
+  cudaError_t outer_residual(const T *b, const T *x) {
+    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+      constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, 1, cs, partials, counter);
+      return cudaGetLastError();
+    });
+  }
+};
+
+template <typename Arith64>
+ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                     const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s) {
+  const int mp = m == 1 ? 1 : (m + 1) / 2 * 2;
+  const int64_t n = M->n;
+  const int singular = (M->flags & ENS_MATRIX_SINGULAR) ? 1 : 0;
+  Scratch sc(s);
+  double *b = nullptr, *x = nullptr;
+  cudaError_t e = sc.get(&b, (size_t)n * mp);
+  if (e == cudaSuccess) e = sc.get(&x, (size_t)n * mp);
+  const int cgrid = M->num_sms * 8;
+  if (e == cudaSuccess) {
+    k_pad<<<cgrid, 256, 0, s>>>(n, m, mp, B, b);
+    if (!o.x0_zero) k_pad<<<cgrid, 256, 0, s>>>(n, m, mp, X, x);
+    e = cudaGetLastError();
+  }
+  std::vector<double> tolv(mp, 0.0);
+  for (int l = 0; l < m; ++l) tolv[l] = tol[l];
+  std::vector<int32_t> iters(mp, 0), status(mp, 0), state(mp, 0), outer(mp, 0);
+  std::vector<double> relres(mp, 0.0);
+
+  if (o.precision == ENS_PREC_F64) {
+    Bicg<Arith64> S;
+    if (e == cudaSuccess) e = S.setup(sc, M, mp, o, s);
+    if (e == cudaSuccess) e = S.start(b, x, o.x0_zero != 0, singular, tolv);
+    int ran = 0;
+    if (e == cudaSuccess) e = S.iterate(x, o.max_iter, o.check_every, &ran);
+    if (e == cudaSuccess) e = S.finish(b, x, singular);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(iters.data(), S.cs.iters, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), S.cs.status, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(state.data(), S.cs.state, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(relres.data(), S.cs.relres, mp * 8, cudaMemcpyDeviceToHost, s);
+  } else {
+    // Outer FP64 loop: r = b - A x, inner FP32 solve of A d = r / ||r||, x += ||r|| d.
+    Bicg<Arith64> O;  // only its residual, scalars and reduction scratch are used
+    Bicg<ArithF32> I;
+    float *r32 = nullptr, *d32 = nullptr;
+    ens_solve_opts oo = o;
+    oo.precond = ENS_PRECOND_NONE;
+    if (e == cudaSuccess) e = O.setup(sc, M, mp, oo, s, true);
+    if (e == cudaSuccess) e = I.setup(sc, M, mp, o, s);
+    if (e == cudaSuccess) e = sc.get(&r32, (size_t)n * mp);
+    if (e == cudaSuccess) e = sc.get(&d32, (size_t)n * mp);
+    if (e == cudaSuccess) e = O.start(b, x, o.x0_zero != 0, singular, tolv);
+    std::vector<float> itol(mp, (float)o.inner_tol);
+    std::vector<int32_t> h, inner_it(mp);
+    for (int k = 0; e == cudaSuccess && k < o.max_outer; ++k) {
+      e = O.states(h);
+      if (e != cudaSuccess || Bicg<Arith64>::all_done(h)) break;
+      e = with_vl(O.vec, O.lanes, [&](auto Vc, auto Lc) {
+        constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+        k_to32<V, L><<<O.grid, kThreads, 0, s>>>((int32_t)n, mp, O.r, r32, O.cs);
+        return cudaGetLastError();
+      });
+      if (e == cudaSuccess) e = I.start(r32, d32, true, 0, itol);
+      int ran = 0;
+      if (e == cudaSuccess) e = I.iterate(d32, o.max_iter, o.check_every, &ran);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(inner_it.data(), I.cs.iters, mp * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) break;
+      for (int l = 0; l < mp; ++l)
+        if (h[l] == ST_ACTIVE) {
+          iters[l] += inner_it[l];
+          outer[l] += 1;
+        }
+      e = with_vl(O.vec, O.lanes, [&](auto Vc, auto Lc) {
+        constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+        k_correct<V, L><<<O.grid, kThreads, 0, s>>>((int32_t)n, mp, x, d32, O.cs);
+        return cudaGetLastError();
+      });
+      if (e == cudaSuccess) e = O.outer_residual(b, x);
+    }
+    if (e == cudaSuccess) e = O.finish(b, x, singular);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), O.cs.status, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(state.data(), O.cs.state, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(relres.data(), O.cs.relres, mp * 8, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) {
+    k_unpad<<<cgrid, 256, 0, s>>>(n, m, mp, x, X);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "solve_block");
+  for (int l = 0; l < m; ++l) {
+    if (state[l] != ST_DONE) status[l] = ENS_COL_MAXITER;
+    if (st) {
+      if (st->iters) st->iters[l] = iters[l];
+      if (st->status) st->status[l] = status[l];
+      if (st->relres) st->relres[l] = relres[l];
+      if (st->outer) st->outer[l] = outer[l];
+    }
+  }
+  return ENS_OK;
+}
+
+
+extern template struct Bicg<ArithF32>;
+extern template struct Bicg<ArithF64Split>;
+extern template struct Bicg<ArithF64Native>;
+
+}  // namespace solver
+}  // namespace ens

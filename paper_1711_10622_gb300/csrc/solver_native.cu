@@ -1,0 +1,13 @@
+// Instantiation of the float64 solver on native DFMA GSpMV arithmetic.
+#include "solver_impl.cuh"
+
+namespace ens {
+namespace solver {
+template struct Bicg<ArithF64Native>;
+
+ens_status solve_f64_native(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                            const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s) {
+  return solve_f64<ArithF64Native>(M, m, B, X, tol, o, st, s);
+}
+}  // namespace solver
+}  // namespace ens
