@@ -212,6 +212,41 @@ def run_reference(args):
     return 0
 
 
+def run_profile(args):
+    """Launch-only mode for ncu captures: W + K GSpMV launches per (m, arithmetic) on a channel
+    operator of the requested size, no timing output. Sizes: 'full' = 256 x 128 x 128, 'half' =
+    128 x 128 x 128 (inputs still larger than L2, a few GB on the device at most)."""
+    import torch
+
+    import gen
+    from paper_1711_10622_gb300 import build as ens_build
+
+    ens_build.build()
+    import paper_1711_10622_gb300 as ens
+
+    dims = {"full": (256, 128, 128), "half": (128, 128, 128)}[args.profile_size]
+    op = gen.channel(*dims)
+    A = ens.Matrix.from_operator(op)
+    ms = [int(v) for v in args.profile_m.split(",")]
+    modes = args.profile_modes.split(",")
+    for m in ms:
+        X = torch.from_numpy(gen.rhs_normal(op.n, m, 20000 + m)).to("cuda")
+        for mode in modes:
+            Xin = X.float() if mode == "f32" else X
+            Y = torch.empty_like(Xin)
+            if mode != "f32":
+                A.set_f64_mode(mode)
+            for _ in range(args.warmup + args.steps):
+                ens.gspmv(A, Xin, Y)
+            torch.cuda.synchronize()
+            del Y, Xin
+        del X
+        torch.cuda.empty_cache()
+    A.close()
+    print(json.dumps({"profile": "gspmv", "size": dims, "m": ms, "modes": modes, "launches_per_case": args.warmup + args.steps}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,7 +256,13 @@ def main():
     ap.add_argument("--f64-mode", default="auto", choices=["auto", "native", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--profile", action="store_true", help="launch-only mode for ncu captures")
+    ap.add_argument("--profile-size", default="half", choices=["half", "full"])
+    ap.add_argument("--profile-m", default="1,8,32")
+    ap.add_argument("--profile-modes", default="split,native,f32")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -179,15 +179,21 @@ __device__ __forceinline__ double widen_f32(float f) {
 // One double addition of the exactly widened parts (the only FP64 instruction per output).
 __device__ __forceinline__ double split_to_double(float hi, float lo) { return widen_f32(hi) + widen_f32(lo); }
 
+// Each column decides on its own whether its split result is valid, so the value of one column
+// never depends on the values of the others (a column solved alone or inside a block gives the
+// same bits).
 template <int VEC>
 __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t *__restrict__ ci,
                                           const float2 *__restrict__ vs, const double *__restrict__ va,
                                           int32_t m, int32_t c, const double *__restrict__ X,
                                           double (&y)[VEC]) {
   float sh[VEC], sl[VEC];
+  bool ok[VEC];
 #pragma unroll
-  for (int q = 0; q < VEC; ++q) sh[q] = sl[q] = 0.f;
-  bool bad = false;
+  for (int q = 0; q < VEC; ++q) {
+    sh[q] = sl[q] = 0.f;
+    ok[q] = true;
+  }
   int32_t j = j0;
   for (; j + kUnroll <= j1; j += kUnroll) {
     int32_t k[kUnroll];
@@ -205,7 +211,7 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
 #pragma unroll
       for (int q = 0; q < VEC; ++q) {
         float xh, xl;
-        bad |= !split_f64(x[u][q], xh, xl);
+        ok[q] &= split_f64(x[u][q], xh, xl);
         split_fma(a[u].x, a[u].y, xh, xl, sh[q], sl[q]);
       }
   }
@@ -217,23 +223,29 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       float xh, xl;
-      bad |= !split_f64(x[q], xh, xl);
+      ok[q] &= split_f64(x[q], xh, xl);
       split_fma(a.x, a.y, xh, xl, sh[q], sl[q]);
     }
   }
-  if (!bad) {
+  bool all_ok = true;
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) y[q] = split_to_double(sh[q], sl[q]);
-  } else {  // values outside the split range: native FP64 for this row segment
+  for (int q = 0; q < VEC; ++q) {
+    y[q] = split_to_double(sh[q], sl[q]);
+    all_ok &= ok[q];
+  }
+  if (!all_ok) {  // values outside the split range: native FP64 for the affected columns
+    double z[VEC];
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) y[q] = 0.0;
+    for (int q = 0; q < VEC; ++q) z[q] = 0.0;
     for (int32_t jj = j0; jj < j1; ++jj) {
       const double av = __ldg(va + jj);
       double x[VEC];
       load_vec<double, VEC>(X + (int64_t)__ldg(ci + jj) * m + c, x);
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) y[q] = fma(av, x[q], y[q]);
+      for (int q = 0; q < VEC; ++q) z[q] = fma(av, x[q], z[q]);
     }
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) y[q] = ok[q] ? y[q] : z[q];
   }
 }
 
