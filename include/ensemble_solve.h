@@ -86,6 +86,14 @@ ens_status ens_matrix_info(const ens_matrix *A, int64_t *n, int64_t *nnz, int32_
 ens_status ens_set_f64_mode(ens_matrix *A, int32_t mode);
 
 /*
+ * Split-float FP64 products only: the share, in 32nds of the row sweeps, that is computed with
+ * native DFMA instead (0 = all split, 32 = all native; -1 = the library's table by block width).
+ * GB300's FP64 pipe is idle in the split path, so a hybrid share adds its throughput. Tuning knob
+ * used by the autotuner; results stay within the FP64 accuracy bound either way.
+ */
+ens_status ens_set_native_share(ens_matrix *A, int32_t share);
+
+/*
  * Generalised SpMV Y = A X (Section 2.3, Fig. GSpMV): for every row i and column l,
  *   Y[i*m + l] = sum_{j = row_ptr[i]}^{row_ptr[i+1]-1} val[j] * X[col_idx[j]*m + l].
  * m >= 1 columns (any m; m in {1,2,4,8,16,32} have specialised kernels). X and Y are DEVICE

@@ -94,6 +94,7 @@ def lib():
         "ens_destroy_matrix": (_i32, [_vp]),
         "ens_matrix_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
         "ens_set_f64_mode": (_i32, [_vp, _i32]),
+        "ens_set_native_share": (_i32, [_vp, _i32]),
         "ens_gspmv": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_gspmv_host": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),

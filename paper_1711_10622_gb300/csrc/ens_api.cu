@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ens_internal.cuh"
+#include "rowprod.cuh"
 
 namespace ens {
 
@@ -140,11 +141,17 @@ ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, con
   cudaError_t e = cudaGetDevice(&A->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&A->num_sms, cudaDevAttrMultiProcessorCount, A->device);
   unsigned *dflags = nullptr;
-  if (e == cudaSuccess) e = dmalloc(&A->row, n + 1);
-  if (e == cudaSuccess) e = dmalloc(&A->col, nnz);
-  if (e == cudaSuccess) e = dmalloc(&A->val, nnz);
-  if (e == cudaSuccess) e = dmalloc(&A->val32, nnz);
-  if (e == cudaSuccess) e = dmalloc(&A->valsplit, nnz);
+  // CSR arrays carry kCsrPad zeroed elements at the end: tiles stage 16-byte rounded segments.
+  if (e == cudaSuccess) e = dmalloc(&A->row, n + 1 + kCsrPad);
+  if (e == cudaSuccess) e = dmalloc(&A->col, nnz + kCsrPad);
+  if (e == cudaSuccess) e = dmalloc(&A->val, nnz + kCsrPad);
+  if (e == cudaSuccess) e = dmalloc(&A->val32, nnz + kCsrPad);
+  if (e == cudaSuccess) e = dmalloc(&A->valsplit, nnz + kCsrPad);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->row + n + 1, 0, kCsrPad * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->col + nnz, 0, kCsrPad * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->val + nnz, 0, kCsrPad * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->val32 + nnz, 0, kCsrPad * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->valsplit + nnz, 0, kCsrPad * sizeof(float2), s);
   if (e == cudaSuccess) e = dmalloc(&A->dinv, n);
   if (e == cudaSuccess) e = dmalloc(&A->dinv32, n);
   if (e == cudaSuccess) e = dmalloc(&dflags, 1);
@@ -194,6 +201,14 @@ ens_status ens_set_f64_mode(ens_matrix *A, int32_t mode) {
   if (!A) return fail(ENS_ERR_INVALID, "set_f64_mode: matrix is NULL");
   if (mode < ENS_F64_AUTO || mode > ENS_F64_SPLIT) return fail(ENS_ERR_INVALID, "set_f64_mode: unknown mode %d", mode);
   A->f64_mode = mode;
+  return ENS_OK;
+}
+
+ens_status ens_set_native_share(ens_matrix *A, int32_t share) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "set_native_share: matrix is NULL");
+  if (share < -1 || share > 32) return fail(ENS_ERR_INVALID, "set_native_share: share %d outside [-1, 32]", share);
+  A->native_share = share;
   return ENS_OK;
 }
 

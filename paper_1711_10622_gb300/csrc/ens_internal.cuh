@@ -24,6 +24,7 @@ struct ens_matrix {
   bool split_ok = false;      // every value lies in the split-float product range
   bool full_diag = false;     // every row has a nonzero diagonal entry
   int32_t f64_mode = ENS_F64_AUTO;
+  int32_t native_share = -1;  // 32nds of row sweeps on native DFMA in split mode (-1: built-in table)
   // staging buffers of ens_gspmv_host (grown on demand)
   void *stage_x = nullptr, *stage_y = nullptr;
   size_t stage_bytes = 0;
@@ -39,6 +40,12 @@ ens_status fail(ens_status st, const char *fmt, ...);
 // Record a CUDA failure (message includes cudaGetErrorString) and return ENS_ERR_CUDA/OOM.
 ens_status cuda_fail(cudaError_t e, const char *what);
 void clear_error();
+
+// Split-float path usable for this matrix (mode, value range, row lengths).
+bool use_split(const ens_matrix *A);
+// Native-DFMA share (32nds of row sweeps) used by the split path for block width m.
+int native_share(const ens_matrix *A, int m);
+uint32_t share_mask(int share);
 
 // Enqueue Y = A X; arguments already validated.
 ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s);

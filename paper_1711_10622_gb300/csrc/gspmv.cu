@@ -29,38 +29,31 @@ MatView view_of(const ens_matrix *A) {
   return MatView{(int32_t)A->n, A->row, A->col, A->val, A->val32, A->valsplit, A->dinv, A->dinv32};
 }
 
-// One row group of LANES threads per row, VEC columns per lane, grid-stride over rows; for
-// m > VEC * LANES each lane loops over column chunks.
+// Tiled GSpMV: CSR segments staged in shared memory (tile_rows), Y written with streaming stores.
 template <typename Arith, int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
-    gspmv_kernel(MatView A, int32_t m, const typename Arith::T *__restrict__ X, typename Arith::T *__restrict__ Y) {
+    gspmv_kernel(MatView A, int32_t m, const typename Arith::T *__restrict__ X, typename Arith::T *__restrict__ Y,
+                 uint32_t native_mask) {
   using T = typename Arith::T;
-  const int lane = threadIdx.x % LANES;
-  const int64_t G = (int64_t)gridDim.x * (kThreads / LANES);
-  for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < A.n; i += G) {
-    for (int32_t c = lane * VEC; c < m; c += LANES * VEC) {
-      T y[VEC];
-      Arith::template row<VEC>(A, i, m, c, X, y);
-      store_vec_cs<T, VEC>(Y + i * m + c, y);
-    }
-  }
+  tile_rows<Arith, VEC, LANES>(A, m, X, native_mask,
+                               [&](int64_t i, int32_t c, const T (&y)[VEC]) { store_vec_cs<T, VEC>(Y + i * m + c, y); });
 }
 
-int grid_for(const ens_matrix *A, int64_t groups_per_block_rows, const void *kernel) {
+int grid_for(const ens_matrix *A, const void *kernel) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (A->n + groups_per_block_rows - 1) / groups_per_block_rows;
+  const int64_t need = (A->n + kTileRows - 1) / kTileRows;
   const int64_t full = (int64_t)A->num_sms * per_sm;
   return (int)(need < full ? need : full);
 }
 
 template <typename Arith, int VEC, int LANES>
-cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, cudaStream_t s) {
+cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, cudaStream_t s) {
   using T = typename Arith::T;
   auto k = gspmv_kernel<Arith, VEC, LANES>;
-  const int grid = grid_for(A, kThreads / LANES, (const void *)k);
-  k<<<grid, kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y);
+  const int grid = grid_for(A, (const void *)k);
+  k<<<grid, kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
   return cudaGetLastError();
 }
 
@@ -74,14 +67,14 @@ bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 // Dispatch on LANES, a power of two in [1, 32].
 template <typename Arith, int VEC>
-cudaError_t dispatch(const ens_matrix *A, int m, const void *X, void *Y, int lanes, cudaStream_t s) {
+cudaError_t dispatch(const ens_matrix *A, int m, const void *X, void *Y, int lanes, uint32_t mask, cudaStream_t s) {
   switch (lanes) {
-    case 1: return run<Arith, VEC, 1>(A, m, X, Y, s);
-    case 2: return run<Arith, VEC, 2>(A, m, X, Y, s);
-    case 4: return run<Arith, VEC, 4>(A, m, X, Y, s);
-    case 8: return run<Arith, VEC, 8>(A, m, X, Y, s);
-    case 16: return run<Arith, VEC, 16>(A, m, X, Y, s);
-    default: return run<Arith, VEC, 32>(A, m, X, Y, s);
+    case 1: return run<Arith, VEC, 1>(A, m, X, Y, mask, s);
+    case 2: return run<Arith, VEC, 2>(A, m, X, Y, mask, s);
+    case 4: return run<Arith, VEC, 4>(A, m, X, Y, mask, s);
+    case 8: return run<Arith, VEC, 8>(A, m, X, Y, mask, s);
+    case 16: return run<Arith, VEC, 16>(A, m, X, Y, mask, s);
+    default: return run<Arith, VEC, 32>(A, m, X, Y, mask, s);
   }
 }
 
@@ -91,23 +84,46 @@ bool use_split(const ens_matrix *A) {
   return A->f64_mode != ENS_F64_NATIVE && A->split_ok && A->max_row_len <= kSplitMaxRow;
 }
 
+// Share (in 32nds) of row sweeps given to native DFMA in split mode, by block width m: the FP64
+// pipe is otherwise idle, so hybrid tiles add its throughput to that of the split path. A value
+// set with ens_set_native_share overrides the table.
+int native_share(const ens_matrix *A, int m) {
+  if (A->native_share >= 0) return A->native_share;
+  if (A->f64_mode == ENS_F64_SPLIT) return 0;
+  if (m <= 1) return 32;
+  return 0;
+}
+
+// Bit s set for about share/32 of the sweep indices s = 0..31, spread evenly.
+uint32_t share_mask(int share) {
+  uint32_t mask = 0;
+  for (int s = 0; s < 32; ++s)
+    if (((s + 1) * share) / 32 > (s * share) / 32) mask |= 1u << s;
+  return mask;
+}
+
 ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s) {
   if (A->n == 0) return ENS_OK;
   cudaError_t e;
   if (dtype == ENS_F32) {
     if (m % 4 == 0 && aligned(X, 16) && aligned(Y, 16))
-      e = dispatch<ArithF32, 4>(A, m, X, Y, pow2_at_least(m / 4, 8), s);
+      e = dispatch<ArithF32, 4>(A, m, X, Y, pow2_at_least(m / 4, 8), 0u, s);
     else if (m % 2 == 0 && aligned(X, 8) && aligned(Y, 8))
-      e = dispatch<ArithF32, 2>(A, m, X, Y, pow2_at_least(m / 2, 16), s);
+      e = dispatch<ArithF32, 2>(A, m, X, Y, pow2_at_least(m / 2, 16), 0u, s);
     else
-      e = dispatch<ArithF32, 1>(A, m, X, Y, pow2_at_least(m, 32), s);
+      e = dispatch<ArithF32, 1>(A, m, X, Y, pow2_at_least(m, 32), 0u, s);
   } else {
     const bool vec2 = (m % 2 == 0) && aligned(X, 16) && aligned(Y, 16);
     const int lanes = vec2 ? pow2_at_least(m / 2, 16) : pow2_at_least(m, 32);
-    if (use_split(A))
-      e = vec2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, lanes, s) : dispatch<ArithF64Split, 1>(A, m, X, Y, lanes, s);
-    else
-      e = vec2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, lanes, s) : dispatch<ArithF64Native, 1>(A, m, X, Y, lanes, s);
+    const int share = use_split(A) ? native_share(A, m) : 32;
+    if (share < 32) {
+      const uint32_t mask = share_mask(share);
+      e = vec2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, lanes, mask, s)
+               : dispatch<ArithF64Split, 1>(A, m, X, Y, lanes, mask, s);
+    } else {
+      e = vec2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, lanes, 0u, s)
+               : dispatch<ArithF64Native, 1>(A, m, X, Y, lanes, 0u, s);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e, "gspmv launch");
   return ENS_OK;

@@ -78,10 +78,10 @@ __device__ __forceinline__ void store_vec_cs(T *p, const T (&v)[VEC]) {
 constexpr int kUnroll = 4;
 
 // ------------------------------------------------------------------ float32 / native float64
-template <typename T, int VEC>
-__device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t *__restrict__ ci,
-                                          const T *__restrict__ va, int32_t m, int32_t c,
-                                          const T *__restrict__ X, T (&acc)[VEC]) {
+// ci/va point either into a shared-memory tile or into global memory; j0, j1 index them.
+template <typename T, typename V, int VEC>
+__device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t *ci, const V *va, int32_t m,
+                                          int32_t c, const T *__restrict__ X, T (&acc)[VEC]) {
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[q] = T(0);
   int32_t j = j0;
@@ -90,8 +90,8 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
     T a[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      k[u] = __ldcs(ci + j + u);
-      a[u] = __ldcs(va + j + u);
+      k[u] = ci[j + u];
+      a[u] = (T)va[j + u];
     }
     T x[kUnroll][VEC];
 #pragma unroll
@@ -102,8 +102,8 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
       for (int q = 0; q < VEC; ++q) acc[q] = fma(a[u], x[u][q], acc[q]);
   }
   for (; j < j1; ++j) {
-    const int32_t k = __ldcs(ci + j);
-    const T a = __ldcs(va + j);
+    const int32_t k = ci[j];
+    const T a = (T)va[j];
     T x[VEC];
     load_vec<T, VEC>(X + (int64_t)k * m + c, x);
 #pragma unroll
@@ -179,14 +179,52 @@ __device__ __forceinline__ double widen_f32(float f) {
 // One double addition of the exactly widened parts (the only FP64 instruction per output).
 __device__ __forceinline__ double split_to_double(float hi, float lo) { return widen_f32(hi) + widen_f32(lo); }
 
-// Each column decides on its own whether its split result is valid, so the value of one column
-// never depends on the values of the others (a column solved alone or inside a block gives the
-// same bits).
+// Packed pairs of floats (f32x2): sm_100-class SMs execute FP32 add/mul/fma on two lanes per
+// instruction, so the two columns a lane owns share every FP32 instruction of the split path.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Native DFMA row product (the split path's fallback and the FP64 share of hybrid tiles).
 template <int VEC>
-__device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t *__restrict__ ci,
-                                          const float2 *__restrict__ vs, const double *__restrict__ va,
-                                          int32_t m, int32_t c, const double *__restrict__ X,
-                                          double (&y)[VEC]) {
+__device__ __forceinline__ void row_native_f64(int32_t j0, int32_t j1, const int32_t *ci, const double *__restrict__ vn,
+                                               int32_t m, int32_t c, const double *__restrict__ X, double (&z)[VEC]) {
+  row_plain<double, double, VEC>(j0, j1, ci, vn, m, c, X, z);
+}
+
+// Split-float row product. ci / vs (hi, lo pairs) are indexed by j in [j0, j1) and point into a
+// shared-memory tile or into global memory; vn is the float64 value array under the same index
+// (global), used when a column's X values leave the split range. Each column decides on its own,
+// so one column's values never change another column's result.
+template <int VEC>
+__device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t *ci, const float2 *vs,
+                                          const double *__restrict__ vn, int32_t m, int32_t c,
+                                          const double *__restrict__ X, double (&y)[VEC]) {
   float sh[VEC], sl[VEC];
   bool ok[VEC];
 #pragma unroll
@@ -194,30 +232,9 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
     sh[q] = sl[q] = 0.f;
     ok[q] = true;
   }
-  int32_t j = j0;
-  for (; j + kUnroll <= j1; j += kUnroll) {
-    int32_t k[kUnroll];
-    float2 a[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      k[u] = __ldcs(ci + j + u);
-      a[u] = __ldcs(vs + j + u);
-    }
-    double x[kUnroll][VEC];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) load_vec<double, VEC>(X + (int64_t)k[u] * m + c, x[u]);
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        float xh, xl;
-        ok[q] &= split_f64(x[u][q], xh, xl);
-        split_fma(a[u].x, a[u].y, xh, xl, sh[q], sl[q]);
-      }
-  }
-  for (; j < j1; ++j) {
-    const int32_t k = __ldcs(ci + j);
-    const float2 a = __ldcs(vs + j);
+  for (int32_t j = j0; j < j1; ++j) {
+    const int32_t k = ci[j];
+    const float2 a = vs[j];
     double x[VEC];
     load_vec<double, VEC>(X + (int64_t)k * m + c, x);
 #pragma unroll
@@ -233,46 +250,181 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
     y[q] = split_to_double(sh[q], sl[q]);
     all_ok &= ok[q];
   }
-  if (!all_ok) {  // values outside the split range: native FP64 for the affected columns
+  if (!all_ok) {
     double z[VEC];
-#pragma unroll
-    for (int q = 0; q < VEC; ++q) z[q] = 0.0;
-    for (int32_t jj = j0; jj < j1; ++jj) {
-      const double av = __ldg(va + jj);
-      double x[VEC];
-      load_vec<double, VEC>(X + (int64_t)__ldg(ci + jj) * m + c, x);
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) z[q] = fma(av, x[q], z[q]);
-    }
+    row_native_f64<VEC>(j0, j1, ci, vn, m, c, X, z);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) y[q] = ok[q] ? y[q] : z[q];
   }
 }
 
-// Arithmetic selectors for kernels templated on the product variant.
+// Two columns per lane: the same arithmetic as split_fma on packed pairs. With p = ah*xh rounded,
+// the negated error terms are accumulated (fma(-ah, xh, p) = p - ah*xh exactly), which needs no
+// packed negation.
+template <>
+__device__ __forceinline__ void row_split<2>(int32_t j0, int32_t j1, const int32_t *ci, const float2 *vs,
+                                             const double *__restrict__ vn, int32_t m, int32_t c,
+                                             const double *__restrict__ X, double (&y)[2]) {
+  uint64_t sh = 0ull, sl = 0ull;
+  bool ok0 = true, ok1 = true;
+#pragma unroll 2
+  for (int32_t j = j0; j < j1; ++j) {
+    const int32_t k = ci[j];
+    const float2 a = vs[j];
+    double x[2];
+    load_vec<double, 2>(X + (int64_t)k * m + c, x);
+    float xh0, xl0, xh1, xl1;
+    ok0 &= split_f64(x[0], xh0, xl0);
+    ok1 &= split_f64(x[1], xh1, xl1);
+    const uint64_t xh = f2_pack(xh0, xh1), xl = f2_pack(xl0, xl1);
+    const uint64_t ah = f2_pack(a.x, a.x), nah = f2_pack(-a.x, -a.x), nal = f2_pack(-a.y, -a.y);
+    const uint64_t ph = f2_mul(ah, xh);
+    uint64_t npl = f2_fma(nah, xh, ph);  // -(ah*xh - ph)
+    npl = f2_fma(nah, xl, npl);
+    npl = f2_fma(nal, xh, npl);          // -(low part of the product)
+    const uint64_t s = f2_add(sh, ph);
+    const uint64_t bb = f2_sub(s, sh);
+    const uint64_t e = f2_add(f2_sub(sh, f2_sub(s, bb)), f2_sub(ph, bb));
+    sh = s;
+    sl = f2_add(sl, f2_sub(e, npl));
+  }
+  float h0, h1, l0, l1;
+  f2_unpack(sh, h0, h1);
+  f2_unpack(sl, l0, l1);
+  y[0] = split_to_double(h0, l0);
+  y[1] = split_to_double(h1, l1);
+  if (!(ok0 && ok1)) {
+    double z[2];
+    row_native_f64<2>(j0, j1, ci, vn, m, c, X, z);
+    y[0] = ok0 ? y[0] : z[0];
+    y[1] = ok1 ? y[1] : z[1];
+  }
+}
+
+// Arithmetic selectors. V is the per-nonzero value type staged in shared memory; row() computes
+// one row segment from CSR arrays indexed by [j0, j1) (shared tile or global), vn being the
+// float64 values under the same index; native forces DFMA (hybrid split/native tiles).
 struct ArithF32 {
   using T = float;
+  using V = float;
+  __device__ __forceinline__ static const V *vals(const MatView &A) { return A.val32; }
   template <int VEC>
-  __device__ __forceinline__ static void row(const MatView &A, int64_t i, int32_t m, int32_t c, const float *X, float (&y)[VEC]) {
-    row_plain<float, VEC>(__ldg(A.rp + i), __ldg(A.rp + i + 1), A.ci, A.val32, m, c, X, y);
+  __device__ __forceinline__ static void row(const int32_t *ci, const V *va, const double *, int32_t j0, int32_t j1,
+                                             int32_t m, int32_t c, const float *X, float (&y)[VEC], bool) {
+    row_plain<float, float, VEC>(j0, j1, ci, va, m, c, X, y);
   }
   __device__ __forceinline__ static float dinv(const MatView &A, int64_t i) { return __ldg(A.dinv32 + i); }
 };
 struct ArithF64Native {
   using T = double;
+  using V = double;
+  __device__ __forceinline__ static const V *vals(const MatView &A) { return A.val; }
   template <int VEC>
-  __device__ __forceinline__ static void row(const MatView &A, int64_t i, int32_t m, int32_t c, const double *X, double (&y)[VEC]) {
-    row_plain<double, VEC>(__ldg(A.rp + i), __ldg(A.rp + i + 1), A.ci, A.val, m, c, X, y);
+  __device__ __forceinline__ static void row(const int32_t *ci, const V *va, const double *, int32_t j0, int32_t j1,
+                                             int32_t m, int32_t c, const double *X, double (&y)[VEC], bool) {
+    row_plain<double, double, VEC>(j0, j1, ci, va, m, c, X, y);
   }
   __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
 };
 struct ArithF64Split {
   using T = double;
+  using V = float2;
+  __device__ __forceinline__ static const V *vals(const MatView &A) { return A.vs; }
   template <int VEC>
-  __device__ __forceinline__ static void row(const MatView &A, int64_t i, int32_t m, int32_t c, const double *X, double (&y)[VEC]) {
-    row_split<VEC>(__ldg(A.rp + i), __ldg(A.rp + i + 1), A.ci, A.vs, A.val, m, c, X, y);
+  __device__ __forceinline__ static void row(const int32_t *ci, const V *va, const double *vn, int32_t j0, int32_t j1,
+                                             int32_t m, int32_t c, const double *X, double (&y)[VEC], bool native) {
+    if (native)
+      row_native_f64<VEC>(j0, j1, ci, vn, m, c, X, y);
+    else
+      row_split<VEC>(j0, j1, ci, va, vn, m, c, X, y);
   }
   __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
 };
+
+// ------------------------------------------------------------------ row tiles
+// A block walks tiles of kTileRows consecutive rows (grid-stride). For each tile it stages the
+// row pointers and the tile's contiguous CSR segment (column indices and values) in shared
+// memory with 16-byte coalesced loads (the arrays are padded so the rounded-out segment stays
+// inside them), then each row group of LANES threads computes rows g, g + G, g + 2G, ... of the
+// tile from shared memory and hands each (row, column chunk) result to the epilogue. A tile
+// whose segment exceeds kTileNnz is computed from global memory instead. native_mask bit
+// (s & 31) sends row sweep s (counted over all tiles) to native DFMA (split arithmetic only), so the
+// FP64 pipe takes a share of the products while the FP32/integer pipes take the rest.
+constexpr int kTileRows = 256;
+constexpr int kTileNnz = 2048;
+constexpr int kCsrPad = 4;  // extra elements allocated after row_ptr, col_idx and every value array
+
+template <typename V>
+struct TileSmem {
+  int32_t rp[kTileRows + 4];
+  int32_t ci[kTileNnz];
+  V va[kTileNnz];
+};
+
+template <typename E>
+__device__ __forceinline__ void stage16(E *dst, const E *__restrict__ src, int32_t count) {
+  // count elements, count * sizeof(E) a multiple of 16, src and dst 16-byte aligned
+  const int32_t n16 = count * (int32_t)sizeof(E) / 16;
+  const int4 *s = reinterpret_cast<const int4 *>(src);
+  int4 *d = reinterpret_cast<int4 *>(dst);
+  for (int32_t t = threadIdx.x; t < n16; t += blockDim.x) d[t] = __ldcs(s + t);
+}
+
+template <typename Arith, int VEC, int LANES, typename Epi>
+__device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typename Arith::T *__restrict__ X,
+                                          uint32_t native_mask, Epi &&epi) {
+  using T = typename Arith::T;
+  using V = typename Arith::V;
+  constexpr int kThr = 256;
+  constexpr int G = kThr / LANES;
+  constexpr int RPG = kTileRows / G;
+  __shared__ __align__(16) TileSmem<V> sm;
+  const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES;
+  const V *gva = Arith::vals(A);
+  for (int64_t r0 = (int64_t)blockIdx.x * kTileRows; r0 < A.n; r0 += (int64_t)gridDim.x * kTileRows) {
+    const int rows = (int)min((int64_t)kTileRows, (int64_t)A.n - r0);
+    stage16<int32_t>(sm.rp, A.rp + r0, (rows + 1 + 3) & ~3);
+    __syncthreads();
+    const int32_t ab = sm.rp[0] & ~3, ae = (sm.rp[rows] + 3) & ~3;
+    const bool staged = ae - ab <= kTileNnz;
+    if (staged) {
+      stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
+      stage16<V>(sm.va, gva + ab, ae - ab);
+    }
+    __syncthreads();
+    const double *vn = A.val + ab;
+    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG;  // sweep counter: spreads native_mask over tiles
+    if (staged) {
+#pragma unroll 1
+      for (int rr = 0; rr < RPG; ++rr) {
+        const int lr = rr * G + grp;
+        if (lr >= rows) break;
+        const int32_t j0 = sm.rp[lr] - ab, j1 = sm.rp[lr + 1] - ab;
+        const bool nat = (native_mask >> ((sweep0 + rr) & 31)) & 1u;
+        for (int32_t c = lane * VEC; c < m; c += LANES * VEC) {
+          T y[VEC];
+          Arith::template row<VEC>(sm.ci, sm.va, vn, j0, j1, m, c, X, y, nat);
+          epi(r0 + lr, c, y);
+        }
+      }
+    } else {
+      const int32_t *gci = A.ci + ab;
+      const V *gv = gva + ab;
+#pragma unroll 1
+      for (int rr = 0; rr < RPG; ++rr) {
+        const int lr = rr * G + grp;
+        if (lr >= rows) break;
+        const int32_t j0 = sm.rp[lr] - ab, j1 = sm.rp[lr + 1] - ab;
+        const bool nat = (native_mask >> ((sweep0 + rr) & 31)) & 1u;
+        for (int32_t c = lane * VEC; c < m; c += LANES * VEC) {
+          T y[VEC];
+          Arith::template row<VEC>(gci, gv, vn, j0, j1, m, c, X, y, nat);
+          epi(r0 + lr, c, y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
 
 }  // namespace ens

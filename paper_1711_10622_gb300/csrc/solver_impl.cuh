@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads)
     k_start(MatView A, int32_t m, const typename Arith::T *__restrict__ b, typename Arith::T *x,
             typename Arith::T *__restrict__ r, typename Arith::T *__restrict__ rh, int x0_zero, int singular,
             typename Arith::T incompat, Cols<typename Arith::T> cs, typename Arith::T *partials,
-            unsigned *counter) {
+            unsigned *counter, uint32_t mask) {
   using T = typename Arith::T;
   const int32_t c = (threadIdx.x % LANES) * VEC;
   T acc[3][VEC];
@@ -79,27 +79,31 @@ __global__ void __launch_bounds__(kThreads)
   for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[d][q] = T(0);
-  if (c < m) {
-    ENS_ROWS(i) {
-      T bv[VEC], ax[VEC], rv[VEC];
-      load_vec<T, VEC>(b + i * m + c, bv);
-      if (x0_zero) {
+  auto fin_row = [&](int64_t i, int32_t cc, const T (&ax)[VEC]) {
+    T bv[VEC], rv[VEC];
+    load_vec<T, VEC>(b + i * m + cc, bv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      rv[q] = bv[q] - ax[q];
+      acc[0][q] += bv[q] * bv[q];
+      acc[1][q] += rv[q] * rv[q];
+      acc[2][q] += bv[q];
+    }
+    store_vec<T, VEC>(r + i * m + cc, rv);
+    if (rh) store_vec<T, VEC>(rh + i * m + cc, rv);
+  };
+  if (x0_zero) {
+    if (c < m) {
+      ENS_ROWS(i) {
+        T ax[VEC];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) ax[q] = T(0);
         store_vec<T, VEC>(x + i * m + c, ax);
-      } else {
-        Arith::template row<VEC>(A, i, m, c, x, ax);
+        fin_row(i, c, ax);
       }
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        rv[q] = bv[q] - ax[q];
-        acc[0][q] += bv[q] * bv[q];
-        acc[1][q] += rv[q] * rv[q];
-        acc[2][q] += bv[q];
-      }
-      store_vec<T, VEC>(r + i * m + c, rv);
-      if (rh) store_vec<T, VEC>(rh + i * m + c, rv);
     }
+  } else {
+    tile_rows<Arith, VEC, LANES>(A, m, x, mask, fin_row);
   }
   reduce_cols<T, 3, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 3> &t) {
     const T bn2 = t.v[0][l], rn2 = t.v[1][l], sb = t.v[2][l];
@@ -183,19 +187,16 @@ template <typename Arith, int VEC, int LANES, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kThreads)
     k_cheb(MatView A, int32_t m, const typename Arith::T *__restrict__ din, typename Arith::T *__restrict__ dout,
            const typename Arith::T *__restrict__ src, typename Arith::T *res, typename Arith::T *z,
-           typename Arith::T c1, typename Arith::T c2) {
+           typename Arith::T c1, typename Arith::T c2, uint32_t mask) {
   using T = typename Arith::T;
-  const int32_t c = (threadIdx.x % LANES) * VEC;
-  if (c >= m) return;
-  ENS_ROWS(i) {
-    T w[VEC], di[VEC], rs[VEC], zv[VEC], dn[VEC];
-    Arith::template row<VEC>(A, i, m, c, din, w);
-    load_vec<T, VEC>(din + i * m + c, di);
+  tile_rows<Arith, VEC, LANES>(A, m, din, mask, [&](int64_t i, int32_t cc, const T (&w)[VEC]) {
+    T di[VEC], rs[VEC], zv[VEC], dn[VEC];
+    load_vec<T, VEC>(din + i * m + cc, di);
     if (FIRST)
-      load_vec<T, VEC>(src + i * m + c, rs);
+      load_vec<T, VEC>(src + i * m + cc, rs);
     else
-      load_vec_rw<T, VEC>(res + i * m + c, rs);
-    load_vec_rw<T, VEC>(z + i * m + c, zv);
+      load_vec_rw<T, VEC>(res + i * m + cc, rs);
+    load_vec_rw<T, VEC>(z + i * m + cc, zv);
     const T dv = Arith::dinv(A, i);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
@@ -203,12 +204,12 @@ __global__ void __launch_bounds__(kThreads)
       dn[q] = c1 * di[q] + c2 * (dv * rs[q]);
       zv[q] += dn[q];
     }
-    store_vec<T, VEC>(z + i * m + c, zv);
+    store_vec<T, VEC>(z + i * m + cc, zv);
     if (!LAST) {
-      store_vec<T, VEC>(res + i * m + c, rs);
-      store_vec<T, VEC>(dout + i * m + c, dn);
+      store_vec<T, VEC>(res + i * m + cc, rs);
+      store_vec<T, VEC>(dout + i * m + cc, dn);
     }
-  }
+  });
 }
 
 // ----------------------------------------------------------------------------- v = A ph
@@ -216,22 +217,18 @@ template <typename Arith, int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
     k_v(MatView A, int32_t m, const typename Arith::T *__restrict__ ph, typename Arith::T *__restrict__ v,
         const typename Arith::T *__restrict__ rh, int32_t it, Cols<typename Arith::T> cs,
-        typename Arith::T *partials, unsigned *counter) {
+        typename Arith::T *partials, unsigned *counter, uint32_t mask) {
   using T = typename Arith::T;
-  const int32_t c = (threadIdx.x % LANES) * VEC;
   T acc[1][VEC];
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[0][q] = T(0);
-  if (c < m) {
-    ENS_ROWS(i) {
-      T y[VEC], h[VEC];
-      Arith::template row<VEC>(A, i, m, c, ph, y);
-      store_vec<T, VEC>(v + i * m + c, y);
-      load_vec<T, VEC>(rh + i * m + c, h);
+  tile_rows<Arith, VEC, LANES>(A, m, ph, mask, [&](int64_t i, int32_t cc, const T (&y)[VEC]) {
+    T h[VEC];
+    store_vec<T, VEC>(v + i * m + cc, y);
+    load_vec<T, VEC>(rh + i * m + cc, h);
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) acc[0][q] += h[q] * y[q];
-    }
-  }
+    for (int q = 0; q < VEC; ++q) acc[0][q] += h[q] * y[q];
+  });
   reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 1> &t) {
     if (cs.state[l] != ST_ACTIVE) return;
     cs.iters[l] = it;
@@ -289,25 +286,21 @@ template <typename Arith, int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
     k_t(MatView A, int32_t m, const typename Arith::T *__restrict__ sh, typename Arith::T *__restrict__ t,
         const typename Arith::T *__restrict__ s, Cols<typename Arith::T> cs, typename Arith::T *partials,
-        unsigned *counter) {
+        unsigned *counter, uint32_t mask) {
   using T = typename Arith::T;
-  const int32_t c = (threadIdx.x % LANES) * VEC;
   T acc[2][VEC];
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[0][q] = acc[1][q] = T(0);
-  if (c < m) {
-    ENS_ROWS(i) {
-      T y[VEC], sv[VEC];
-      Arith::template row<VEC>(A, i, m, c, sh, y);
-      store_vec<T, VEC>(t + i * m + c, y);
-      load_vec<T, VEC>(s + i * m + c, sv);
+  tile_rows<Arith, VEC, LANES>(A, m, sh, mask, [&](int64_t i, int32_t cc, const T (&y)[VEC]) {
+    T sv[VEC];
+    store_vec<T, VEC>(t + i * m + cc, y);
+    load_vec<T, VEC>(s + i * m + cc, sv);
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        acc[0][q] += y[q] * sv[q];
-        acc[1][q] += y[q] * y[q];
-      }
+    for (int q = 0; q < VEC; ++q) {
+      acc[0][q] += y[q] * sv[q];
+      acc[1][q] += y[q] * y[q];
     }
-  }
+  });
   reduce_cols<T, 2, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 2> &tt) {
     if (cs.state[l] != ST_ACTIVE) return;
     const T t2 = tt.v[1][l];
@@ -450,25 +443,21 @@ template <typename Arith, int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
     k_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ b, const typename Arith::T *__restrict__ x,
             typename Arith::T *__restrict__ r, int outer, Cols<typename Arith::T> cs, typename Arith::T *partials,
-            unsigned *counter) {
+            unsigned *counter, uint32_t mask) {
   using T = typename Arith::T;
-  const int32_t c = (threadIdx.x % LANES) * VEC;
   T acc[1][VEC];
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[0][q] = T(0);
-  if (c < m) {
-    ENS_ROWS(i) {
-      T y[VEC], bv[VEC];
-      Arith::template row<VEC>(A, i, m, c, x, y);
-      load_vec<T, VEC>(b + i * m + c, bv);
+  tile_rows<Arith, VEC, LANES>(A, m, x, mask, [&](int64_t i, int32_t cc, const T (&ax)[VEC]) {
+    T y[VEC], bv[VEC];
+    load_vec<T, VEC>(b + i * m + cc, bv);
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        y[q] = bv[q] - y[q];
-        acc[0][q] += y[q] * y[q];
-      }
-      if (r) store_vec<T, VEC>(r + i * m + c, y);
+    for (int q = 0; q < VEC; ++q) {
+      y[q] = bv[q] - ax[q];
+      acc[0][q] += y[q] * y[q];
     }
-  }
+    if (r) store_vec<T, VEC>(r + i * m + cc, y);
+  });
   reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 1> &t) {
     const T rr = t.v[0][l];
     if (outer) {
@@ -610,6 +599,7 @@ struct Bicg {
   int mp = 0, vec = 2, lanes = 1, grid = 0;
   bool prec = false;
   int cheb_steps = 4;
+  uint32_t mask = 0;  // native-DFMA sweeps of the split arithmetic (hybrid tiles)
   double theta = 1, delta = 1;
   cudaStream_t s = nullptr;
   T *r, *rh, *p, *v, *ph, *s_, *sh, *t, *da, *db, *res;
@@ -623,6 +613,7 @@ struct Bicg {
     A = view_of(M);
     n = M->n;
     mp = mp_;
+    mask = std::is_same<Arith, ArithF64Split>::value ? share_mask(native_share(M, mp_)) : 0u;
     s = st;
     vec = mp == 1 ? 1 : 2;
     lanes = 1;
@@ -670,7 +661,7 @@ struct Bicg {
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       k_start<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
-                                                     partials, counter);
+                                                     partials, counter, mask);
       return cudaGetLastError();
     });
   }
@@ -686,13 +677,13 @@ struct Bicg {
       const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta);
       const bool first = k == 1, last = k == cheb_steps - 1;
       if (first && last)
-        k_cheb<Arith, V, L, true, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+        k_cheb<Arith, V, L, true, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (first)
-        k_cheb<Arith, V, L, true, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+        k_cheb<Arith, V, L, true, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (last)
-        k_cheb<Arith, V, L, false, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+        k_cheb<Arith, V, L, false, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else
-        k_cheb<Arith, V, L, false, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2);
+        k_cheb<Arith, V, L, false, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       std::swap(din, dout);
       rho_prev = rho;
     }
@@ -708,14 +699,14 @@ struct Bicg {
       } else {
         k_p<Arith, V, L, false><<<grid, kThreads, 0, s>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
       }
-      k_v<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, ph, v, rh, it, cs, partials, counter);
+      k_v<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, ph, v, rh, it, cs, partials, counter, mask);
       if (prec) {
         k_s<Arith, V, L, true><<<grid, kThreads, 0, s>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
         cheb<V, L>(s_, sh);
       } else {
         k_s<Arith, V, L, false><<<grid, kThreads, 0, s>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
       }
-      k_t<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, sh, t, s_, cs, partials, counter);
+      k_t<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, sh, t, s_, cs, partials, counter, mask);
       k_xr<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, ph, sh, s_, t, r, rh, it, max_iter, cs, partials, counter);
       return cudaGetLastError();
     });
@@ -760,7 +751,7 @@ struct Bicg {
         k_colsum<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, (T)(1.0 / (double)n), cs, partials, counter);
       }
       k_fix<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, singular, cs);
-      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, nullptr, 0, cs, partials, counter);
+      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, nullptr, 0, cs, partials, counter, mask);
       return cudaGetLastError();
     });
   }
@@ -768,7 +759,7 @@ struct Bicg {
   cudaError_t outer_residual(const T *b, const T *x) {
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, 1, cs, partials, counter);
+      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, 1, cs, partials, counter, mask);
       return cudaGetLastError();
     });
   }
