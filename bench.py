@@ -161,6 +161,62 @@ def cpu_baseline_sweep(op, seconds_cap: float = 30.0):
     }
 
 
+def solve_metrics(reps: int = 2):
+    """RHS-solves/s of the block solver against the one-RHS-at-a-time FP64 solver (the same
+    library, m = 1, looped over the columns) on the configured solve workloads. Each solve is
+    timed end to end around the synchronous ens_solve_block call (inputs resident on the GPU)."""
+    import torch
+
+    import gen
+    import paper_1711_10622_gb300 as ens
+
+    cases = [
+        ("dirichlet32_m4", gen.WORKLOADS["dirichlet32_m4"], 4, "none"),
+        ("cubes192x128x96_m8", gen.WORKLOADS["cubes192x128x96_m8"], 8, "chebyshev"),
+    ]
+    out = {}
+    for name, w, m, pre in cases:
+        op = w["op"]()
+        B = torch.from_numpy(w["rhs"](op.n, m)).cuda()
+        tol = w["tol"]
+        A = ens.Matrix.from_operator(op)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                r = fn()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None or dt < best else best
+            return best, r
+
+        res = {}
+        for prec in ("f64", "mixed"):
+            t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tol, precond=pre, precision=prec))
+            res[prec] = {
+                "solves_per_s": m / t,
+                "seconds": t,
+                "max_relres": float(st["relres"].max()),
+                "converged": int((st["status"] == 0).sum()),
+                "iters": st["iters"].tolist(),
+                "outer": st["outer"].tolist(),
+            }
+        cols = [B[:, l : l + 1].contiguous() for l in range(m)]
+        t1, outs = timed(lambda: [ens.solve_block(A, c, tol=tol, precond=pre, precision="f64") for c in cols])
+        base = m / t1
+        res["one_rhs_f64"] = {"solves_per_s": base, "seconds": t1, "iters": [int(o[1]["iters"][0]) for o in outs]}
+        for prec in ("f64", "mixed"):
+            res[prec]["speedup_vs_one_rhs_f64"] = res[prec]["solves_per_s"] / base
+        res["tol"] = tol
+        res["precond"] = pre
+        out[name] = res
+        A.close()
+    return out
+
+
 def run_reference(args):
     """The CPU oracle as it stands, on a bounded row sample of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -236,6 +292,7 @@ def run_profile(args):
             Y = torch.empty_like(Xin)
             if mode != "f32":
                 A.set_f64_mode(mode)
+                ens.api.N.check(ens.api.N.lib().ens_set_native_share(A.handle, args.profile_share if mode == "split" else -1))
             for _ in range(args.warmup + args.steps):
                 ens.gspmv(A, Xin, Y)
             torch.cuda.synchronize()
@@ -255,11 +312,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--f64-mode", default="auto", choices=["auto", "native", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solves", action="store_true", help="skip the solve-throughput section")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--profile", action="store_true", help="launch-only mode for ncu captures")
     ap.add_argument("--profile-size", default="half", choices=["half", "full"])
     ap.add_argument("--profile-m", default="1,8,32")
     ap.add_argument("--profile-modes", default="split,native,f32")
+    ap.add_argument("--profile-share", type=int, default=-1, help="native-DFMA share (32nds) for split mode")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
@@ -391,6 +450,8 @@ def main():
         "api": "ens_gspmv_host (pinned host X/Y)",
     }
 
+    solves = None if args.no_solves else solve_metrics()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sweep(op)
@@ -420,6 +481,7 @@ def main():
             "roofline": roofline,
             "sweep": sweep,
             "e2e": e2e,
+            "solves": solves,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": K * len(M_SWEEP),

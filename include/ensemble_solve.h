@@ -126,8 +126,11 @@ typedef struct {
                           reductions, FP64 outer residual r = b - A x and correction x += d */
   double inner_tol;    /* mixed: relative residual of each FP32 inner solve (default 1e-4) */
   int32_t max_outer;   /* mixed: refinement steps (default 30) */
-  int32_t check_every; /* iterations between host reads of the convergence flags (default 1) */
+  int32_t check_every; /* host-driven loop only: iterations between reads of the convergence flags
+                          (default 1) */
   int32_t x0_zero;     /* nonzero: ignore X on input and start from x0 = 0 */
+  int32_t use_graph;   /* nonzero (default): the iteration loop runs on the device as a CUDA graph
+                          with a conditional WHILE node; 0: host-driven loop */
 } ens_solve_opts;
 
 /* Host arrays of m entries each, filled on return; any pointer may be NULL. */

@@ -50,6 +50,7 @@ class SolveOpts(ctypes.Structure):
         ("max_outer", ctypes.c_int32),
         ("check_every", ctypes.c_int32),
         ("x0_zero", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
     ]
 
 

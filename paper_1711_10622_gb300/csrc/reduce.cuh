@@ -26,9 +26,14 @@ struct ColTotals {
 // acc[d][q]: this thread's sum for dot d and column lane*VEC + q (zero for idle lanes).
 // partials: gridDim.x * ND * m scratch values; counter: zero before the launch, reset to zero by
 // the last block. fin(l, totals) runs on threads l < m of the last block.
-template <typename T, int ND, int VEC, int LANES, typename Fin>
+struct NoAfter {
+  __device__ void operator()() const {}
+};
+
+// after(): runs once, on thread 0 of the last block, when every column's fin() has finished.
+template <typename T, int ND, int VEC, int LANES, typename Fin, typename After = NoAfter>
 __device__ __forceinline__ void reduce_cols(T (&acc)[ND][VEC], int32_t m, T *__restrict__ partials,
-                                            unsigned *__restrict__ counter, Fin &&fin) {
+                                            unsigned *__restrict__ counter, Fin &&fin, After &&after = After()) {
   constexpr int kWarps = kThreads / 32;
   __shared__ T sm[kWarps][ND][kMaxSolveM];
   __shared__ ColTotals<T, ND> tot;
@@ -72,7 +77,11 @@ __device__ __forceinline__ void reduce_cols(T (&acc)[ND][VEC], int32_t m, T *__r
   }
   __syncthreads();
   if ((int)threadIdx.x < m) fin((int)threadIdx.x, tot);
-  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    after();
+    *counter = 0u;
+  }
 }
 
 }  // namespace ens

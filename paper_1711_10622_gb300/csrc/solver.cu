@@ -66,6 +66,7 @@ void ens_default_solve_opts(ens_solve_opts *o) {
   o->max_outer = 30;
   o->check_every = 1;
   o->x0_zero = 0;
+  o->use_graph = 1;
 }
 
 ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,

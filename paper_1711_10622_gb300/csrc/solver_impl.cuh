@@ -47,6 +47,7 @@ struct Cols {
   T *rho, *rho_old, *alpha, *omega, *bn2, *thr2, *rh2, *rn2, *tol, *mean;
   int32_t *state, *iters, *status, *flags;
   double *relres;
+  int32_t *it;  // [2]: iterations completed, "go" flag (some column active and it < max_iter)
 };
 
 template <typename T>
@@ -135,6 +136,11 @@ __global__ void __launch_bounds__(kThreads)
     cs.status[l] = status;
     cs.flags[l] = fl;
     cs.iters[l] = 0;
+  }, [&]() {
+    int32_t any = 0;
+    for (int l = 0; l < m; ++l) any |= cs.state[l] != ST_DONE;
+    cs.it[0] = 0;
+    cs.it[1] = any;
   });
 }
 
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename Arith, int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
     k_v(MatView A, int32_t m, const typename Arith::T *__restrict__ ph, typename Arith::T *__restrict__ v,
-        const typename Arith::T *__restrict__ rh, int32_t it, Cols<typename Arith::T> cs,
+        const typename Arith::T *__restrict__ rh, Cols<typename Arith::T> cs,
         typename Arith::T *partials, unsigned *counter, uint32_t mask) {
   using T = typename Arith::T;
   T acc[1][VEC];
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(kThreads)
   });
   reduce_cols<T, 1, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 1> &t) {
     if (cs.state[l] != ST_ACTIVE) return;
-    cs.iters[l] = it;
+    cs.iters[l] = cs.it[0] + 1;
     const T rv = t.v[0][l];
     if (rv == T(0)) {
       cs.state[l] = ST_DONE;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kThreads)
     k_xr(MatView A, int32_t m, typename Arith::T *x, const typename Arith::T *__restrict__ ph,
          const typename Arith::T *__restrict__ sh, const typename Arith::T *__restrict__ s,
          const typename Arith::T *__restrict__ t, typename Arith::T *__restrict__ r,
-         const typename Arith::T *__restrict__ rh, int32_t it, int32_t max_iter, Cols<typename Arith::T> cs,
+         const typename Arith::T *__restrict__ rh, int32_t max_iter, Cols<typename Arith::T> cs,
          typename Arith::T *partials, unsigned *counter) {
   using T = typename Arith::T;
   const int32_t c = (threadIdx.x % LANES) * VEC;
@@ -354,6 +360,7 @@ __global__ void __launch_bounds__(kThreads)
       store_vec<T, VEC>(r + i * m + c, sv);
     }
   }
+  const int32_t it = cs.it[0] + 1;  // the iteration this launch completes
   reduce_cols<T, 2, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 2> &tt) {
     const int st = cs.state[l];
     if (st == ST_HALF) {
@@ -387,7 +394,17 @@ __global__ void __launch_bounds__(kThreads)
         cs.rho[l] = rr;
       }
     }
+  }, [&]() {
+    int32_t any = 0;
+    for (int l = 0; l < m; ++l) any |= cs.state[l] != ST_DONE;
+    cs.it[0] = it;
+    cs.it[1] = any && it < max_iter;
   });
+}
+
+// Loop condition of the device-driven iteration graph (a conditional WHILE node).
+static __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int32_t *__restrict__ it) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, it[1] ? 1u : 0u);
 }
 
 // ----------------------------------------------------------------------------- finishing
@@ -586,6 +603,7 @@ cudaError_t alloc_cols(Scratch &sc, int m, Cols<T> &cs) {
   for (int32_t **p : ip)
     if (e == cudaSuccess) e = sc.get(p, m);
   if (e == cudaSuccess) e = sc.get(&cs.relres, m);
+  if (e == cudaSuccess) e = sc.get(&cs.it, 2);
   return e;
 }
 
@@ -668,7 +686,7 @@ struct Bicg {
 
   // Chebyshev application z = p(D^-1 A) D^-1 src; the first term is already in da and z.
   template <int V, int L>
-  void cheb(const T *src, T *z) {
+  void cheb(const T *src, T *z, cudaStream_t st) {
     const double sigma = theta / delta;
     double rho_prev = 1.0 / sigma;
     T *din = da, *dout = db;
@@ -677,37 +695,39 @@ struct Bicg {
       const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta);
       const bool first = k == 1, last = k == cheb_steps - 1;
       if (first && last)
-        k_cheb<Arith, V, L, true, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, true, true><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (first)
-        k_cheb<Arith, V, L, true, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, true, false><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (last)
-        k_cheb<Arith, V, L, false, true><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, false, true><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else
-        k_cheb<Arith, V, L, false, false><<<grid, kThreads, 0, s>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, false, false><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       std::swap(din, dout);
       rho_prev = rho;
     }
   }
 
-  cudaError_t iteration(T *x, int it, int max_iter) {
+  // One BiCGStab iteration for every column (frozen columns are no-ops); the iteration number
+  // lives on the device, so the same launches can be captured once and replayed.
+  cudaError_t iteration(T *x, int max_iter, cudaStream_t st) {
     const T inv_theta = (T)(1.0 / theta);
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       if (prec) {
-        k_p<Arith, V, L, true><<<grid, kThreads, 0, s>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
-        cheb<V, L>(p, ph);
+        k_p<Arith, V, L, true><<<grid, kThreads, 0, st>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
+        cheb<V, L>(p, ph, st);
       } else {
-        k_p<Arith, V, L, false><<<grid, kThreads, 0, s>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
+        k_p<Arith, V, L, false><<<grid, kThreads, 0, st>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
       }
-      k_v<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, ph, v, rh, it, cs, partials, counter, mask);
+      k_v<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, ph, v, rh, cs, partials, counter, mask);
       if (prec) {
-        k_s<Arith, V, L, true><<<grid, kThreads, 0, s>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
-        cheb<V, L>(s_, sh);
+        k_s<Arith, V, L, true><<<grid, kThreads, 0, st>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
+        cheb<V, L>(s_, sh, st);
       } else {
-        k_s<Arith, V, L, false><<<grid, kThreads, 0, s>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
+        k_s<Arith, V, L, false><<<grid, kThreads, 0, st>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
       }
-      k_t<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, sh, t, s_, cs, partials, counter, mask);
-      k_xr<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, ph, sh, s_, t, r, rh, it, max_iter, cs, partials, counter);
+      k_t<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, sh, t, s_, cs, partials, counter, mask);
+      k_xr<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, ph, sh, s_, t, r, rh, max_iter, cs, partials, counter);
       return cudaGetLastError();
     });
   }
@@ -725,23 +745,82 @@ struct Bicg {
     return true;
   }
 
-  // Iterate until every column is done or max_iter; returns the iterations run.
-  cudaError_t iterate(T *x, int max_iter, int check_every, int *ran) {
+  cudaError_t iterations_run(int *ran) {
+    int32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, cs.it, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *ran = h;
+    return e;
+  }
+
+  // Host-driven loop: launch iterations, read the column states every check_every iterations.
+  cudaError_t iterate_host(T *x, int max_iter, int check_every, int *ran) {
     std::vector<int32_t> h;
     cudaError_t e = states(h);
     *ran = 0;
     if (e != cudaSuccess || all_done(h)) return e;
     for (int it = 1; it <= max_iter; ++it) {
-      e = iteration(x, it, max_iter);
+      e = iteration(x, max_iter, s);
       if (e != cudaSuccess) return e;
-      *ran = it;
       if (it % check_every == 0 || it == max_iter) {
         e = states(h);
         if (e != cudaSuccess) return e;
         if (all_done(h)) break;
       }
     }
-    return cudaSuccess;
+    return iterations_run(ran);
+  }
+
+  // Device-driven loop: one iteration is captured as the body of a conditional WHILE graph node
+  // whose condition (some column active and fewer than max_iter iterations) is set on the device
+  // by k_loop_cond; one graph launch runs the whole solve with no host round trip. The loop ends
+  // after at most max_iter iterations.
+  cudaError_t iterate_graph(T *x, int max_iter, int *ran) {
+    *ran = 0;
+    if (max_iter <= 0) return cudaSuccess;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle h{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+      if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t ek = iteration(x, max_iter, cap);
+      if (ek == cudaSuccess) {
+        k_loop_cond<<<1, 32, 0, cap>>>(h, cs.it);
+        ek = cudaGetLastError();
+      }
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(cap, &captured);
+      if (e == cudaSuccess) e = ek;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    // skip the launch when every column finished in the start phase
+    std::vector<int32_t> st;
+    if (e == cudaSuccess) e = states(st);
+    if (e == cudaSuccess && !all_done(st)) e = cudaGraphLaunch(ge, s);
+    if (e == cudaSuccess) e = iterations_run(ran);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (cap) cudaStreamDestroy(cap);
+    return e;
+  }
+
+  cudaError_t iterate(T *x, int max_iter, int check_every, bool graph, int *ran) {
+    return graph ? iterate_graph(x, max_iter, ran) : iterate_host(x, max_iter, check_every, ran);
   }
 
   cudaError_t finish(const T *b, T *x, int singular) {
@@ -791,7 +870,7 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
     if (e == cudaSuccess) e = S.setup(sc, M, mp, o, s);
     if (e == cudaSuccess) e = S.start(b, x, o.x0_zero != 0, singular, tolv);
     int ran = 0;
-    if (e == cudaSuccess) e = S.iterate(x, o.max_iter, o.check_every, &ran);
+    if (e == cudaSuccess) e = S.iterate(x, o.max_iter, o.check_every, o.use_graph != 0, &ran);
     if (e == cudaSuccess) e = S.finish(b, x, singular);
     if (e == cudaSuccess) e = cudaMemcpyAsync(iters.data(), S.cs.iters, mp * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), S.cs.status, mp * 4, cudaMemcpyDeviceToHost, s);
@@ -821,7 +900,7 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
       });
       if (e == cudaSuccess) e = I.start(r32, d32, true, 0, itol);
       int ran = 0;
-      if (e == cudaSuccess) e = I.iterate(d32, o.max_iter, o.check_every, &ran);
+      if (e == cudaSuccess) e = I.iterate(d32, o.max_iter, o.check_every, o.use_graph != 0, &ran);
       if (e == cudaSuccess) e = cudaMemcpyAsync(inner_it.data(), I.cs.iters, mp * 4, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) break;
