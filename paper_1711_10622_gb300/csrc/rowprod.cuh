@@ -79,11 +79,42 @@ constexpr int kUnroll = 4;
 
 // ------------------------------------------------------------------ float32 / native float64
 // ci/va point either into a shared-memory tile or into global memory; j0, j1 index them.
+// Rows of up to kShortRow nonzeros (every row of a 7-point operator) issue all their X loads at
+// once (predicated), so a row costs one L2 round trip; longer rows loop in groups of kUnroll.
+constexpr int kShortRow = 8;
+
 template <typename T, typename V, int VEC>
 __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t *ci, const V *va, int32_t m,
                                           int32_t c, const T *__restrict__ X, T (&acc)[VEC]) {
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[q] = T(0);
+  const int32_t len = j1 - j0;
+  if (len <= kShortRow) {
+    int32_t k[kShortRow];
+    T a[kShortRow];
+    T x[kShortRow][VEC];
+#pragma unroll
+    for (int u = 0; u < kShortRow; ++u) {
+      const bool v = u < len;
+      k[u] = v ? ci[j0 + u] : 0;
+      a[u] = v ? (T)va[j0 + u] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kShortRow; ++u) {
+      if (u < len) {
+        load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) x[u][q] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kShortRow; ++u)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q)
+        if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
+    return;
+  }
   int32_t j = j0;
   for (; j + kUnroll <= j1; j += kUnroll) {
     int32_t k[kUnroll];
@@ -393,7 +424,10 @@ __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typ
     }
     __syncthreads();
     const double *vn = A.val + ab;
-    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG;  // sweep counter: spreads native_mask over tiles
+    // sweep counter: spreads native_mask over tiles; the per-warp rotation keeps warps of one SM in
+    // different phases so the FP64 pipe (native sweeps) and the FP32/integer pipes (split sweeps)
+    // work at the same time
+    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG + (threadIdx.x >> 5) * 5u + blockIdx.x;
     if (staged) {
 #pragma unroll 1
       for (int rr = 0; rr < RPG; ++rr) {
