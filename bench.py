@@ -359,6 +359,8 @@ def main():
     for m in M_SWEEP:
         Xs[m] = torch.from_numpy(gen.rhs_normal(n, m, 20000 + m)).to("cuda")
         Ys[m] = torch.empty_like(Xs[m])
+    # launch configuration per width picked by the library's autotuner (set-up, not timed)
+    tuned = {m: A.autotune(m, "f64") for m in M_SWEEP} if args.f64_mode == "auto" else {}
 
     def step(evs=None):
         for m in M_SWEEP:
@@ -419,6 +421,7 @@ def main():
             "alg_mb": alg_bytes(n, nnz, m) / 1e6,
             "paper_sigma_mb": paper_traffic(n, nnz, m) / 1e6,
             "gain_vs_m1": m * per_m_us[1] / per_m_us[m],
+            "tuned": tuned.get(m),
         }
         for m in M_SWEEP
     }

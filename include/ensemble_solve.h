@@ -94,6 +94,17 @@ ens_status ens_set_f64_mode(ens_matrix *A, int32_t mode);
 ens_status ens_set_native_share(ens_matrix *A, int32_t share);
 
 /*
+ * Autotuner: time the GSpMV launch candidates for block width m (1..64) and dtype on this matrix
+ * (lanes per row, i.e. rows per warp and column-tile width; for FP64 also native DFMA vs split-float
+ * with native shares 0, 8, 16, 24 of 32) and keep the fastest for later ens_gspmv calls and for the
+ * solver's products of that width. Uses temporary device blocks of n x m (stream-ordered, freed
+ * before return). Synchronous. Optional outputs: chosen lanes, chosen share (32 = native), and the
+ * best time per launch in microseconds. A share set with ens_set_native_share still takes priority.
+ */
+ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, int32_t *lanes, int32_t *share,
+                        double *best_us);
+
+/*
  * Generalised SpMV Y = A X (Section 2.3, Fig. GSpMV): for every row i and column l,
  *   Y[i*m + l] = sum_{j = row_ptr[i]}^{row_ptr[i+1]-1} val[j] * X[col_idx[j]*m + l].
  * m >= 1 columns (any m; m in {1,2,4,8,16,32} have specialised kernels). X and Y are DEVICE

@@ -75,7 +75,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree library, or the file named by ENSEMBLE_SOLVE_LIB (to load another build)."""
+    return os.environ.get("ENSEMBLE_SOLVE_LIB") or _build.LIB
 
 
 def lib():
@@ -96,6 +97,10 @@ def lib():
         "ens_matrix_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
         "ens_set_f64_mode": (_i32, [_vp, _i32]),
         "ens_set_native_share": (_i32, [_vp, _i32]),
+        "ens_autotune": (
+            _i32,
+            [_vp, _i32, _i32, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)],
+        ),
         "ens_gspmv": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_gspmv_host": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),

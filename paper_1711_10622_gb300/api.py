@@ -82,6 +82,19 @@ class Matrix:
         code = {"auto": N.ENS_F64_AUTO, "native": N.ENS_F64_NATIVE, "split": N.ENS_F64_SPLIT}[mode]
         N.check(N.lib().ens_set_f64_mode(self.handle, code))
 
+    def set_native_share(self, share: int):
+        """Split-float FP64: 32nds of row sweeps on native DFMA (-1: library table/autotuner)."""
+        N.check(N.lib().ens_set_native_share(self.handle, int(share)))
+
+    def autotune(self, m: int, dtype: str = "f64", stream=None) -> dict:
+        """Time the GSpMV candidates for width m and keep the fastest (ens_autotune)."""
+        lanes, share, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        code = {"f64": N.ENS_F64, "f32": N.ENS_F32}[dtype]
+        N.check(
+            N.lib().ens_autotune(self.handle, int(m), code, _stream_handle(stream), ctypes.byref(lanes), ctypes.byref(share), ctypes.byref(us))
+        )
+        return {"m": int(m), "dtype": dtype, "lanes": lanes.value, "share": share.value, "best_us": us.value}
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             N.check(N.lib().ens_destroy_matrix(self._h))

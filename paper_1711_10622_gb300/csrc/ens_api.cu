@@ -212,6 +212,15 @@ ens_status ens_set_native_share(ens_matrix *A, int32_t share) {
   return ENS_OK;
 }
 
+ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, int32_t *lanes, int32_t *share,
+                        double *best_us) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "autotune: matrix is NULL");
+  if (m < 1 || m > kTuneMaxM) return fail(ENS_ERR_INVALID, "autotune: m = %d outside [1, %d]", m, kTuneMaxM);
+  if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "autotune: unknown dtype %d", dtype);
+  return autotune(A, m, dtype, (cudaStream_t)stream, lanes, share, best_us);
+}
+
 ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream) {
   clear_error();
   ens_status st = check_gspmv_args(A, m, dtype, X, Y);

@@ -8,6 +8,8 @@
 
 #include "ensemble_solve.h"
 
+constexpr int kTuneMaxM = 64;  // block widths the autotuner keeps a choice for
+
 struct ens_matrix {
   int64_t n = 0, nnz = 0;
   int32_t max_row_len = 0;
@@ -25,6 +27,12 @@ struct ens_matrix {
   bool full_diag = false;     // every row has a nonzero diagonal entry
   int32_t f64_mode = ENS_F64_AUTO;
   int32_t native_share = -1;  // 32nds of row sweeps on native DFMA in split mode (-1: built-in table)
+  // autotuned launch choices by block width m (-1: none): lanes per row [0: FP64, 1: FP32], share
+  int8_t tuned_lanes[2][kTuneMaxM + 1];
+  int8_t tuned_share[kTuneMaxM + 1];
+  ens_matrix() {
+    for (int i = 0; i <= kTuneMaxM; ++i) tuned_lanes[0][i] = tuned_lanes[1][i] = tuned_share[i] = -1;
+  }
   // staging buffers of ens_gspmv_host (grown on demand)
   void *stage_x = nullptr, *stage_y = nullptr;
   size_t stage_bytes = 0;
@@ -46,6 +54,10 @@ bool use_split(const ens_matrix *A);
 // Native-DFMA share (32nds of row sweeps) used by the split path for block width m.
 int native_share(const ens_matrix *A, int m);
 uint32_t share_mask(int share);
+
+// Time the launch candidates for block width m and keep the fastest (synchronous).
+ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *lanes_out, int32_t *share_out,
+                    double *best_us_out);
 
 // Enqueue Y = A X; arguments already validated.
 ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s);

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "ens_internal.cuh"
 #include "rowprod.cuh"
@@ -90,6 +91,7 @@ bool use_split(const ens_matrix *A) {
 int native_share(const ens_matrix *A, int m) {
   if (A->native_share >= 0) return A->native_share;
   if (A->f64_mode == ENS_F64_SPLIT) return 0;
+  if (m >= 1 && m <= kTuneMaxM && A->tuned_share[m] >= 0) return A->tuned_share[m];
   // Measured on GB300 (channel 256 x 128 x 128): native DFMA is fastest up to m = 2; beyond, half
   // of the row sweeps on the FP64 pipe and half split is fastest (m = 32: 1213 us against 1444 us
   // all split and 1710 us all native).
@@ -105,30 +107,147 @@ uint32_t share_mask(int share) {
   return mask;
 }
 
-ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s) {
-  if (A->n == 0) return ENS_OK;
-  cudaError_t e;
+namespace {
+
+// Launch configuration of one product: VEC from m and alignment; lanes per row (rows per warp =
+// 32 / lanes, column tile = VEC * lanes); share of native-DFMA sweeps (FP64 only).
+struct Cfg {
+  int vec, lanes, share;
+};
+
+Cfg default_cfg(const ens_matrix *A, int m, int dtype, const void *X, const void *Y) {
+  Cfg c{};
   if (dtype == ENS_F32) {
-    if (m % 4 == 0 && aligned(X, 16) && aligned(Y, 16))
-      e = dispatch<ArithF32, 4>(A, m, X, Y, pow2_at_least(m / 4, 8), 0u, s);
-    else if (m % 2 == 0 && aligned(X, 8) && aligned(Y, 8))
-      e = dispatch<ArithF32, 2>(A, m, X, Y, pow2_at_least(m / 2, 16), 0u, s);
-    else
-      e = dispatch<ArithF32, 1>(A, m, X, Y, pow2_at_least(m, 32), 0u, s);
+    if (m % 4 == 0 && aligned(X, 16) && aligned(Y, 16)) {
+      c.vec = 4;
+      c.lanes = pow2_at_least(m / 4, 8);
+    } else if (m % 2 == 0 && aligned(X, 8) && aligned(Y, 8)) {
+      c.vec = 2;
+      c.lanes = pow2_at_least(m / 2, 16);
+    } else {
+      c.vec = 1;
+      c.lanes = pow2_at_least(m, 32);
+    }
+    c.share = 0;
   } else {
     const bool vec2 = (m % 2 == 0) && aligned(X, 16) && aligned(Y, 16);
-    const int lanes = vec2 ? pow2_at_least(m / 2, 16) : pow2_at_least(m, 32);
-    const int share = use_split(A) ? native_share(A, m) : 32;
-    if (share < 32) {
-      const uint32_t mask = share_mask(share);
-      e = vec2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, lanes, mask, s)
-               : dispatch<ArithF64Split, 1>(A, m, X, Y, lanes, mask, s);
+    c.vec = vec2 ? 2 : 1;
+    c.lanes = vec2 ? pow2_at_least(m / 2, 16) : pow2_at_least(m, 32);
+    c.share = use_split(A) ? native_share(A, m) : 32;
+  }
+  if (m >= 1 && m <= kTuneMaxM) {
+    const int tl = A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m];
+    if (tl > 0 && tl <= c.lanes) c.lanes = tl;  // tuned for the same VEC (alignment permitting)
+  }
+  return c;
+}
+
+cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, void *Y, const Cfg &c, cudaStream_t s) {
+  if (dtype == ENS_F32) {
+    if (c.vec == 4) return dispatch<ArithF32, 4>(A, m, X, Y, c.lanes, 0u, s);
+    if (c.vec == 2) return dispatch<ArithF32, 2>(A, m, X, Y, c.lanes, 0u, s);
+    return dispatch<ArithF32, 1>(A, m, X, Y, c.lanes, 0u, s);
+  }
+  if (c.share < 32) {
+    const uint32_t mask = share_mask(c.share);
+    return c.vec == 2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, c.lanes, mask, s)
+                      : dispatch<ArithF64Split, 1>(A, m, X, Y, c.lanes, mask, s);
+  }
+  return c.vec == 2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, c.lanes, 0u, s)
+                    : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, s);
+}
+
+// Deterministic N(0,1)-like fill of the tuning block (values in the split range, no zeros).
+__global__ void k_tune_fill(int64_t count, double *x, float *x32) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)(e * 2654435761ull) ^ 0x9E3779B9u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    const float v = 0.25f + (float)(h & 0xFFFFFF) * (1.0f / 16777216.0f);  // [0.25, 1.25)
+    const float sgn = (h & 0x80000000u) ? -1.f : 1.f;
+    if (x) x[e] = (double)(sgn * v);
+    if (x32) x32[e] = sgn * v;
+  }
+}
+
+}  // namespace
+
+ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s) {
+  if (A->n == 0) return ENS_OK;
+  const Cfg c = default_cfg(A, m, dtype, X, Y);
+  cudaError_t e = launch_cfg(A, m, dtype, X, Y, c, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gspmv launch");
+  return ENS_OK;
+}
+
+// Autotuner: time every candidate (lanes per row: full, half and quarter column tile; FP64
+// arithmetic: native DFMA and split with native shares 0, 8, 16, 24) on this matrix for block width
+// m with CUDA events, keep the fastest in the matrix's table.
+ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *lanes_out, int32_t *share_out,
+                    double *best_us_out) {
+  const size_t count = (size_t)A->n * m;
+  void *X = nullptr, *Y = nullptr;
+  const size_t es = dtype == ENS_F32 ? 4 : 8;
+  cudaError_t e = cudaMallocAsync(&X, count * es, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Y, count * es, s);
+  if (e == cudaSuccess) {
+    const int grid = A->num_sms * 8;
+    k_tune_fill<<<grid, 256, 0, s>>>((int64_t)count, dtype == ENS_F32 ? nullptr : (double *)X,
+                                     dtype == ENS_F32 ? (float *)X : nullptr);
+    e = cudaGetLastError();
+  }
+  // the defaults without any previous tuning
+  const int keep_lanes = A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m], keep_share = A->tuned_share[m];
+  A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m] = -1;
+  if (dtype != ENS_F32) A->tuned_share[m] = -1;
+  const Cfg base = default_cfg(A, m, dtype, X, Y);
+  std::vector<Cfg> cand;
+  for (int div = 1; div <= 4; div *= 2) {
+    const int lanes = base.lanes / div;
+    if (lanes < 1) break;
+    if (dtype == ENS_F32) {
+      cand.push_back(Cfg{base.vec, lanes, 0});
     } else {
-      e = vec2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, lanes, 0u, s)
-               : dispatch<ArithF64Native, 1>(A, m, X, Y, lanes, 0u, s);
+      cand.push_back(Cfg{base.vec, lanes, 32});
+      if (use_split(A))
+        for (int sh : {0, 8, 16, 24}) cand.push_back(Cfg{base.vec, lanes, sh});
     }
   }
-  if (e != cudaSuccess) return cuda_fail(e, "gspmv launch");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best = 1e30f;
+  Cfg bestc = base;
+  for (const Cfg &c : cand) {
+    if (e != cudaSuccess) break;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_cfg(A, m, dtype, X, Y, c, s);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_cfg(A, m, dtype, X, Y, c, s);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      bestc = c;
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (X) cudaFreeAsync(X, s);
+  if (Y) cudaFreeAsync(Y, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m] = keep_lanes;
+    A->tuned_share[m] = keep_share;
+    return cuda_fail(e, "autotune");
+  }
+  A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m] = bestc.lanes;
+  if (dtype != ENS_F32) A->tuned_share[m] = bestc.share;
+  if (lanes_out) *lanes_out = bestc.lanes;
+  if (share_out) *share_out = bestc.share;
+  if (best_us_out) *best_us_out = best * 1e3 / 5.0;
   return ENS_OK;
 }
 

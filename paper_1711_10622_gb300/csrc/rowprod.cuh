@@ -79,28 +79,32 @@ constexpr int kUnroll = 4;
 
 // ------------------------------------------------------------------ float32 / native float64
 // ci/va point either into a shared-memory tile or into global memory; j0, j1 index them.
-// Rows of up to kShortRow nonzeros (every row of a 7-point operator) issue all their X loads at
-// once (predicated), so a row costs one L2 round trip; longer rows loop in groups of kUnroll.
-constexpr int kShortRow = 8;
-
+// Nonzeros are processed kUnroll at a time (all X loads of a group in flight together); the last
+// partial group is issued as one predicated group of kUnroll, so a 7-nonzero row costs two L2
+// round trips instead of four.
+#ifndef ENS_ROW_TAIL
+#define ENS_ROW_TAIL 2
+#endif
 template <typename T, typename V, int VEC>
 __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t *ci, const V *va, int32_t m,
                                           int32_t c, const T *__restrict__ X, T (&acc)[VEC]) {
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[q] = T(0);
-  const int32_t len = j1 - j0;
-  if (len <= kShortRow) {
-    int32_t k[kShortRow];
-    T a[kShortRow];
-    T x[kShortRow][VEC];
+#if ENS_ROW_TAIL == 1
+  constexpr int kW = 8;
+  if (j1 - j0 <= kW) {
+    const int32_t len = j1 - j0;
+    int32_t k[kW];
+    T a[kW];
+    T x[kW][VEC];
 #pragma unroll
-    for (int u = 0; u < kShortRow; ++u) {
+    for (int u = 0; u < kW; ++u) {
       const bool v = u < len;
       k[u] = v ? ci[j0 + u] : 0;
       a[u] = v ? (T)va[j0 + u] : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < kShortRow; ++u) {
+    for (int u = 0; u < kW; ++u) {
       if (u < len) {
         load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
       } else {
@@ -109,12 +113,13 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
       }
     }
 #pragma unroll
-    for (int u = 0; u < kShortRow; ++u)
+    for (int u = 0; u < kW; ++u)
 #pragma unroll
       for (int q = 0; q < VEC; ++q)
         if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
     return;
   }
+#endif
   int32_t j = j0;
   for (; j + kUnroll <= j1; j += kUnroll) {
     int32_t k[kUnroll];
@@ -132,6 +137,34 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
 #pragma unroll
       for (int q = 0; q < VEC; ++q) acc[q] = fma(a[u], x[u][q], acc[q]);
   }
+#if ENS_ROW_TAIL == 2
+  if (j < j1) {
+    const int32_t len = j1 - j;
+    int32_t k[kUnroll];
+    T a[kUnroll];
+    T x[kUnroll][VEC];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool v = u < len;
+      k[u] = v ? ci[j + u] : 0;
+      a[u] = v ? (T)va[j + u] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (u < len) {
+        load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) x[u][q] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q)
+        if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
+  }
+#else
   for (; j < j1; ++j) {
     const int32_t k = ci[j];
     const T a = (T)va[j];
@@ -140,6 +173,7 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = fma(a, x[q], acc[q]);
   }
+#endif
 }
 
 // ------------------------------------------------------------------ split float64
@@ -427,7 +461,10 @@ __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typ
     // sweep counter: spreads native_mask over tiles; the per-warp rotation keeps warps of one SM in
     // different phases so the FP64 pipe (native sweeps) and the FP32/integer pipes (split sweeps)
     // work at the same time
-    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG + (threadIdx.x >> 5) * 5u + blockIdx.x;
+#ifndef ENS_PHASE_ROT
+#define ENS_PHASE_ROT 1
+#endif
+    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG + ENS_PHASE_ROT * ((threadIdx.x >> 5) * 5u + blockIdx.x);
     if (staged) {
 #pragma unroll 1
       for (int rr = 0; rr < RPG; ++rr) {

@@ -214,3 +214,33 @@ def test_full_size_channel_sampled(ens, m):
             assert np.all(np.abs(colsum) <= 1e-10 * total)
         Y32 = ens.gspmv(A, Xd.float())[torch.from_numpy(rows).cuda()].double().cpu().numpy()
         assert np.all(np.abs(Y32 - ref) <= 1e-5 * scale)
+
+
+@pytest.mark.parametrize("share", [0, 8, 16, 24, 32])
+def test_hybrid_native_share_parity(ens, share):
+    """Every split/native mix of the FP64 product stays within the FP64 bound."""
+    op = _op("cubes48x32x24")
+    for m in (2, 8, 32):
+        X = gen.rhs_normal(op.n, m, 300 + m)
+        with ens.Matrix.from_operator(op) as A:
+            A.set_native_share(share)
+            Y = ens.gspmv(A, torch.from_numpy(X).cuda()).cpu().numpy()
+        _check_f64(op, X, Y)
+
+
+def test_autotune_then_parity(ens):
+    op = _op("channel20x14x10")
+    with ens.Matrix.from_operator(op) as A:
+        for m in (1, 4, 8, 32):
+            for dt in ("f64", "f32"):
+                r = A.autotune(m, dt)
+                assert r["lanes"] >= 1 and r["best_us"] > 0
+                assert r["share"] in (0, 8, 16, 24, 32) or dt == "f32"
+                X = gen.rhs_normal(op.n, m, 500 + m)
+                if dt == "f64":
+                    Y = ens.gspmv(A, torch.from_numpy(X).cuda()).cpu().numpy()
+                    _check_f64(op, X, Y)
+                else:
+                    X32 = X.astype(np.float32)
+                    Y = ens.gspmv(A, torch.from_numpy(X32).cuda()).cpu().numpy()
+                    _check_f32(op, X32, Y)
