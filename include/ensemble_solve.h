@@ -175,6 +175,26 @@ void ens_default_solve_opts(ens_solve_opts *o);
 ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
                            const ens_solve_opts *opts, ens_solve_stats *stats, void *stream);
 
+/* One system of a batched solve. */
+typedef struct {
+  const ens_matrix *A;    /* its matrix */
+  int32_t m;              /* its block width, 1..64 */
+  const double *B;        /* DEVICE n x m right-hand sides */
+  double *X;              /* DEVICE n x m: initial guess in (unless opts->x0_zero), solution out */
+  const double *tol;      /* HOST [m] */
+  ens_solve_stats *stats; /* HOST arrays of m entries each, or NULL */
+} ens_batch_item;
+
+/*
+ * Solve several systems of uneven n and m at once (Section 2.2's shared-matrix solves, for several
+ * matrices). Each system runs exactly the ens_solve_block algorithm with the shared opts; all of
+ * them are recorded as branches of ONE CUDA graph whose iteration loops are conditional WHILE
+ * nodes (nested outer/inner loops in mixed precision), so a single graph launch runs every system
+ * concurrently and each loop stops on the device when its columns are done or its limit is hit.
+ * The items' buffers must not overlap. Synchronous. Errors name the offending item.
+ */
+ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_solve_opts *opts, void *stream);
+
 /* Human-readable message of the last failed call on this host thread ("" if none). */
 const char *ens_last_error(void);
 

@@ -6,6 +6,6 @@ dot products and a Chebyshev polynomial preconditioner. The computation lives in
 library libensemble_solve.so (include/ensemble_solve.h); this package is its Python binding.
 """
 
-from .api import COL_STATUS, EnsError, Matrix, gspmv, gspmv_host, solve_block, solve_opts, version  # noqa: F401
+from .api import COL_STATUS, EnsError, Matrix, gspmv, gspmv_host, solve_batch, solve_block, solve_opts, version  # noqa: F401
 
-__all__ = ["Matrix", "EnsError", "gspmv", "gspmv_host", "solve_block", "solve_opts", "COL_STATUS", "version"]
+__all__ = ["Matrix", "EnsError", "gspmv", "gspmv_host", "solve_block", "solve_batch", "solve_opts", "COL_STATUS", "version"]

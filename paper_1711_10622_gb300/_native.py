@@ -65,6 +65,19 @@ class SolveStats(ctypes.Structure):
     ]
 
 
+class BatchItem(ctypes.Structure):
+    """Mirror of ens_batch_item."""
+
+    _fields_ = [
+        ("A", ctypes.c_void_p),
+        ("m", ctypes.c_int32),
+        ("B", ctypes.c_void_p),
+        ("X", ctypes.c_void_p),
+        ("tol", ctypes.c_void_p),
+        ("stats", ctypes.POINTER(SolveStats)),
+    ]
+
+
 class EnsError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -108,6 +121,7 @@ def lib():
             _i32,
             [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp],
         ),
+        "ens_solve_batch": (_i32, [_i32, ctypes.POINTER(BatchItem), ctypes.POINTER(SolveOpts), _vp]),
         "ens_last_error": (ctypes.c_char_p, []),
         "ens_version": (ctypes.c_char_p, []),
     }

@@ -225,5 +225,56 @@ def solve_block(A: Matrix, B, X=None, tol=1e-8, stream=None, **opts):
     return X, {"iters": iters, "relres": relres, "status": status, "outer": outer}
 
 
+def _stats_arrays(m):
+    iters = np.zeros(m, dtype=np.int32)
+    relres = np.zeros(m, dtype=np.float64)
+    status = np.zeros(m, dtype=np.int32)
+    outer = np.zeros(m, dtype=np.int32)
+    st = N.SolveStats(
+        iters.ctypes.data_as(ctypes.c_void_p),
+        relres.ctypes.data_as(ctypes.c_void_p),
+        status.ctypes.data_as(ctypes.c_void_p),
+        outer.ctypes.data_as(ctypes.c_void_p),
+    )
+    return st, {"iters": iters, "relres": relres, "status": status, "outer": outer}
+
+
+def solve_batch(systems, stream=None, **opts):
+    """Solve several systems at once (ens_solve_batch: one CUDA graph launch).
+
+    systems: list of (Matrix, B, X or None, tol). B: (n, m) float64 CUDA tensor; X (same shape) is the
+    initial guess and receives the solution (None: a zero initial guess in a new tensor).
+    Returns a list of (X, stats) in the order given.
+    """
+    import torch
+
+    items = (N.BatchItem * len(systems))()
+    keep = []
+    out = []
+    for i, (A, B, X, tol) in enumerate(systems):
+        _check_block(A, B, "B")
+        if B.dtype != torch.float64:
+            raise TypeError("B must be float64")
+        m = B.shape[1]
+        if X is None:
+            X = torch.zeros_like(B)
+        _check_block(A, X, "X")
+        if X.dtype != torch.float64 or X.shape != B.shape:
+            raise ValueError("X must be a float64 tensor shaped like B")
+        tolv = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), (m,)))
+        st, d = _stats_arrays(m)
+        keep += [tolv, st]
+        items[i].A = A.handle
+        items[i].m = m
+        items[i].B = B.data_ptr()
+        items[i].X = X.data_ptr()
+        items[i].tol = tolv.ctypes.data
+        items[i].stats = ctypes.pointer(st)
+        out.append((X, d))
+    o = solve_opts(**opts)
+    N.check(N.lib().ens_solve_batch(len(systems), items, ctypes.byref(o), _stream_handle(stream)))
+    return out
+
+
 def version() -> str:
     return N.lib().ens_version().decode()

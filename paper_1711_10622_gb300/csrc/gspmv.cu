@@ -92,10 +92,11 @@ int native_share(const ens_matrix *A, int m) {
   if (A->native_share >= 0) return A->native_share;
   if (A->f64_mode == ENS_F64_SPLIT) return 0;
   if (m >= 1 && m <= kTuneMaxM && A->tuned_share[m] >= 0) return A->tuned_share[m];
-  // Measured on GB300 (channel 256 x 128 x 128): native DFMA is fastest up to m = 2; beyond, half
-  // of the row sweeps on the FP64 pipe and half split is fastest (m = 32: 1213 us against 1444 us
-  // all split and 1710 us all native).
+  // Measured on GB300 (channel 256 x 128 x 128): native DFMA is fastest up to m = 2; beyond, about
+  // 12/32 of the row sweeps on the FP64 pipe (16/32 from m = 32) and the rest split is fastest
+  // (m = 32: 1148 us against 1461 us all split and 1723 us all native).
   if (m <= 2) return 32;
+  if (m < 32) return 12;
   return 16;
 }
 

@@ -79,47 +79,17 @@ constexpr int kUnroll = 4;
 
 // ------------------------------------------------------------------ float32 / native float64
 // ci/va point either into a shared-memory tile or into global memory; j0, j1 index them.
-// Nonzeros are processed kUnroll at a time (all X loads of a group in flight together); the last
-// partial group is issued as one predicated group of kUnroll, so a 7-nonzero row costs two L2
-// round trips instead of four.
-#ifndef ENS_ROW_TAIL
-#define ENS_ROW_TAIL 2
-#endif
+// Nonzeros are processed kUnroll at a time (all X loads of a group in flight together). For float
+// data the last partial group is issued as one predicated group (a 7-nonzero row costs two L2
+// round trips instead of four); for double data the extra registers of that form cost more
+// occupancy than they save (measured on GB300: native m = 2, 129 us against 159 us), so the tail
+// is processed one nonzero at a time.
 template <typename T, typename V, int VEC>
 __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t *ci, const V *va, int32_t m,
                                           int32_t c, const T *__restrict__ X, T (&acc)[VEC]) {
+  constexpr bool kGroupTail = sizeof(T) == 4;
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[q] = T(0);
-#if ENS_ROW_TAIL == 1
-  constexpr int kW = 8;
-  if (j1 - j0 <= kW) {
-    const int32_t len = j1 - j0;
-    int32_t k[kW];
-    T a[kW];
-    T x[kW][VEC];
-#pragma unroll
-    for (int u = 0; u < kW; ++u) {
-      const bool v = u < len;
-      k[u] = v ? ci[j0 + u] : 0;
-      a[u] = v ? (T)va[j0 + u] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kW; ++u) {
-      if (u < len) {
-        load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) x[u][q] = T(0);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kW; ++u)
-#pragma unroll
-      for (int q = 0; q < VEC; ++q)
-        if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
-    return;
-  }
-#endif
   int32_t j = j0;
   for (; j + kUnroll <= j1; j += kUnroll) {
     int32_t k[kUnroll];
@@ -137,43 +107,43 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
 #pragma unroll
       for (int q = 0; q < VEC; ++q) acc[q] = fma(a[u], x[u][q], acc[q]);
   }
-#if ENS_ROW_TAIL == 2
-  if (j < j1) {
-    const int32_t len = j1 - j;
-    int32_t k[kUnroll];
-    T a[kUnroll];
-    T x[kUnroll][VEC];
+  if (kGroupTail) {
+    if (j < j1) {
+      const int32_t len = j1 - j;
+      int32_t k[kUnroll];
+      T a[kUnroll];
+      T x[kUnroll][VEC];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const bool v = u < len;
-      k[u] = v ? ci[j + u] : 0;
-      a[u] = v ? (T)va[j + u] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      if (u < len) {
-        load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) x[u][q] = T(0);
+      for (int u = 0; u < kUnroll; ++u) {
+        const bool v = u < len;
+        k[u] = v ? ci[j + u] : 0;
+        a[u] = v ? (T)va[j + u] : T(0);
       }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (u < len) {
+          load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) x[u][q] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q)
+          if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
     }
+  } else {
+    for (; j < j1; ++j) {
+      const int32_t k = ci[j];
+      const T a = (T)va[j];
+      T x[VEC];
+      load_vec<T, VEC>(X + (int64_t)k * m + c, x);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-      for (int q = 0; q < VEC; ++q)
-        if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
+      for (int q = 0; q < VEC; ++q) acc[q] = fma(a, x[q], acc[q]);
+    }
   }
-#else
-  for (; j < j1; ++j) {
-    const int32_t k = ci[j];
-    const T a = (T)va[j];
-    T x[VEC];
-    load_vec<T, VEC>(X + (int64_t)k * m + c, x);
-#pragma unroll
-    for (int q = 0; q < VEC; ++q) acc[q] = fma(a, x[q], acc[q]);
-  }
-#endif
 }
 
 // ------------------------------------------------------------------ split float64
@@ -461,10 +431,7 @@ __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typ
     // sweep counter: spreads native_mask over tiles; the per-warp rotation keeps warps of one SM in
     // different phases so the FP64 pipe (native sweeps) and the FP32/integer pipes (split sweeps)
     // work at the same time
-#ifndef ENS_PHASE_ROT
-#define ENS_PHASE_ROT 1
-#endif
-    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG + ENS_PHASE_ROT * ((threadIdx.x >> 5) * 5u + blockIdx.x);
+    const uint32_t sweep0 = (uint32_t)(r0 / kTileRows) * RPG + (threadIdx.x >> 5) * 5u + blockIdx.x;
     if (staged) {
 #pragma unroll 1
       for (int rr = 0; rr < RPG; ++rr) {

@@ -4,9 +4,13 @@
 
 #include <cmath>
 #include <cstdint>
+#include <string>
+
+#include <memory>
+#include <vector>
 
 #include "ens_internal.cuh"
-#include "reduce.cuh"
+#include "solver_impl.cuh"
 
 namespace ens {
 
@@ -67,6 +71,72 @@ void ens_default_solve_opts(ens_solve_opts *o) {
   o->check_every = 1;
   o->x0_zero = 0;
   o->use_graph = 1;
+}
+
+ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_solve_opts *opts, void *stream) {
+  clear_error();
+  if (nsys < 1 || !items) return fail(ENS_ERR_INVALID, "solve_batch: need nsys >= 1 items");
+  ens_solve_opts o;
+  ens_default_solve_opts(&o);
+  if (opts) o = *opts;
+  for (int32_t i = 0; i < nsys; ++i) {
+    const ens_batch_item &it = items[i];
+    ens_status st = validate_solve(it.A, it.m, it.B, it.X, it.tol, o);
+    if (st != ENS_OK) {
+      const std::string msg = ens_last_error();
+      return fail(st, "solve_batch: item %d: %s", i, msg.c_str());
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<std::unique_ptr<solver::SysBase>> sys;
+  for (int32_t i = 0; i < nsys; ++i) {
+    const ens_batch_item &it = items[i];
+    sys.emplace_back(use_split(it.A) ? solver::make_system_split(it.A, it.m, it.B, it.X, it.tol, o, s)
+                                     : solver::make_system_native(it.A, it.m, it.B, it.X, it.tol, o, s));
+  }
+  cudaError_t e = cudaSuccess;
+  {
+    solver::Scratch sc(s);
+    for (auto &p : sys)
+      if (e == cudaSuccess) e = p->setup(sc);
+    // one graph: a branch per system forked from and joined into a private capture stream
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> br(nsys, nullptr);
+    std::vector<cudaEvent_t> ev(nsys + 1, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int32_t i = 0; i < nsys && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    for (int32_t i = 0; i <= nsys && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t ek = cudaEventRecord(ev[nsys], cap);
+      for (int32_t i = 0; i < nsys && ek == cudaSuccess; ++i) {
+        ek = cudaStreamWaitEvent(br[i], ev[nsys], 0);
+        if (ek == cudaSuccess) ek = sys[i]->record(br[i]);
+        if (ek == cudaSuccess) ek = cudaEventRecord(ev[i], br[i]);
+        if (ek == cudaSuccess) ek = cudaStreamWaitEvent(cap, ev[i], 0);
+      }
+      e = cudaStreamEndCapture(cap, &g);
+      if (e == cudaSuccess) e = ek;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+    for (auto &p : sys)
+      if (e == cudaSuccess) e = p->fetch();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    for (cudaStream_t x : br)
+      if (x) cudaStreamDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+  for (int32_t i = 0; i < nsys; ++i) sys[i]->write(items[i].stats);
+  return ENS_OK;
 }
 
 ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,

@@ -669,19 +669,30 @@ struct Bicg {
     return e;
   }
 
-  cudaError_t start(const T *b, T *x, bool x0_zero, int singular, const std::vector<T> &tol) {
-    cudaError_t e = cudaMemcpyAsync(cs.tol, tol.data(), mp * sizeof(T), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    if (p) e = cudaMemsetAsync(p, 0, (size_t)n * mp * sizeof(T), s);
-    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, (size_t)n * mp * sizeof(T), s);
+  // Per-column tolerances to the device (a host copy: done before any graph capture).
+  cudaError_t upload_tol(const std::vector<T> &tol) {
+    return cudaMemcpyAsync(cs.tol, tol.data(), mp * sizeof(T), cudaMemcpyHostToDevice, s);
+  }
+
+  // r = b - A x, rhat = r, p = v = 0, column statuses (capturable: memsets and one kernel).
+  cudaError_t enqueue_start(const T *b, T *x, bool x0_zero, int singular, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (p) e = cudaMemsetAsync(p, 0, (size_t)n * mp * sizeof(T), st);
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, (size_t)n * mp * sizeof(T), st);
     if (e != cudaSuccess) return e;
     const T incompat = (T)(1e-10 * std::sqrt((double)n));
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-      k_start<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
-                                                     partials, counter, mask);
+      k_start<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
+                                                      partials, counter, mask);
       return cudaGetLastError();
     });
+  }
+
+  cudaError_t start(const T *b, T *x, bool x0_zero, int singular, const std::vector<T> &tol) {
+    cudaError_t e = upload_tol(tol);
+    if (e == cudaSuccess) e = enqueue_start(b, x, x0_zero, singular, s);
+    return e;
   }
 
   // Chebyshev application z = p(D^-1 A) D^-1 src; the first term is already in da and z.
@@ -823,22 +834,24 @@ struct Bicg {
     return graph ? iterate_graph(x, max_iter, ran) : iterate_host(x, max_iter, check_every, ran);
   }
 
-  cudaError_t finish(const T *b, T *x, int singular) {
+  cudaError_t finish(const T *b, T *x, int singular, cudaStream_t st = nullptr) {
+    if (!st) st = s;
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       if (singular) {
-        k_colsum<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, (T)(1.0 / (double)n), cs, partials, counter);
+        k_colsum<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, (T)(1.0 / (double)n), cs, partials, counter);
       }
-      k_fix<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, x, singular, cs);
-      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, nullptr, 0, cs, partials, counter, mask);
+      k_fix<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, singular, cs);
+      k_resid<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, b, x, nullptr, 0, cs, partials, counter, mask);
       return cudaGetLastError();
     });
   }
 
-  cudaError_t outer_residual(const T *b, const T *x) {
+  cudaError_t outer_residual(const T *b, const T *x, cudaStream_t st = nullptr) {
+    if (!st) st = s;
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-      k_resid<Arith, V, L><<<grid, kThreads, 0, s>>>(A, mp, b, x, r, 1, cs, partials, counter, mask);
+      k_resid<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, b, x, r, 1, cs, partials, counter, mask);
       return cudaGetLastError();
     });
   }
@@ -939,6 +952,257 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
   return ENS_OK;
 }
 
+
+// ============================================================================= batched solves
+// Every system's whole solve (padding, start, iteration loop, finish) is stream-captured into one
+// branch of a single CUDA graph; the iteration loops are conditional WHILE nodes inserted into the
+// capture (nested outer/inner loops in mixed precision). One graph launch then runs all systems
+// concurrently, each loop ending on the device when its columns are done or its limit is reached.
+
+static __global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned v) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, v);
+}
+
+// Mixed precision, after an inner solve: columns still active in the outer loop add the inner
+// iterations and one refinement step to their counts.
+static __global__ void k_accum(int32_t mp, const int32_t *__restrict__ outer_state, const int32_t *__restrict__ inner_iters,
+                               int32_t *iters_tot, int32_t *outer_cnt) {
+  for (int l = threadIdx.x; l < mp; l += blockDim.x)
+    if (outer_state[l] == ST_ACTIVE) {
+      iters_tot[l] += inner_iters[l];
+      outer_cnt[l] += 1;
+    }
+}
+
+// Outer loop condition: some column still active and fewer than max_outer refinement steps.
+static __global__ void k_outer_cond(cudaGraphConditionalHandle h, int32_t mp, const int32_t *__restrict__ state,
+                                    int32_t *steps, int32_t max_outer) {
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int l = 0; l < mp; ++l) any |= state[l] != ST_DONE;
+    const int k = ++steps[0];
+    cudaGraphSetConditional(h, (any && k < max_outer) ? 1u : 0u);
+  }
+}
+
+// Inside an active capture on `cap`: append a conditional WHILE node (handle created on the
+// capturing graph, default 1) after the current capture dependencies, make it the new dependency
+// and return its (empty) body graph.
+inline cudaError_t capture_while(cudaStream_t cap, cudaGraphConditionalHandle *h, cudaGraph_t *body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cap, &cst, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cst != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  e = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Captures `fill(stream)` into the given (empty) graph on a private stream.
+template <typename F>
+cudaError_t capture_into(cudaGraph_t body, F &&fill) {
+  cudaStream_t c = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(c, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t ef = fill(c);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(c, &out);
+    if (e == cudaSuccess) e = ef;
+  }
+  cudaStreamDestroy(c);
+  return e;
+}
+
+struct SysBase {
+  virtual ~SysBase() {}
+  virtual cudaError_t setup(Scratch &sc) = 0;        // allocations and host-to-device uploads
+  virtual cudaError_t record(cudaStream_t cap) = 0;  // the whole solve, captured
+  virtual cudaError_t fetch() = 0;                   // stats to host (after the graph ran)
+  virtual void write(ens_solve_stats *st) = 0;
+};
+
+template <typename Arith64>
+struct SysImpl : SysBase {
+  const ens_matrix *M;
+  int32_t m, mp;
+  const double *B;
+  double *X;
+  ens_solve_opts o;
+  int singular;
+  cudaStream_t s;
+  double *b = nullptr, *x = nullptr;
+  Bicg<Arith64> S;  // FP64 solver, or the outer residual/scalars in mixed mode
+  Bicg<ArithF32> I; // mixed mode: FP32 inner solver
+  float *r32 = nullptr, *d32 = nullptr;
+  int32_t *iters_tot = nullptr, *outer_cnt = nullptr, *steps = nullptr;
+  std::vector<double> tolv;
+  std::vector<float> itol;
+  std::vector<int32_t> h_iters, h_status, h_state, h_outer;
+  std::vector<double> h_relres;
+
+  SysImpl(const ens_matrix *M_, int32_t m_, const double *B_, double *X_, const double *tol, const ens_solve_opts &o_,
+          cudaStream_t s_)
+      : M(M_), m(m_), B(B_), X(X_), o(o_), s(s_) {
+    mp = m == 1 ? 1 : (m + 1) / 2 * 2;
+    singular = (M->flags & ENS_MATRIX_SINGULAR) ? 1 : 0;
+    tolv.assign(mp, 0.0);
+    for (int l = 0; l < m; ++l) tolv[l] = tol[l];
+    itol.assign(mp, (float)o.inner_tol);
+  }
+
+  bool mixed() const { return o.precision == ENS_PREC_MIXED; }
+
+  cudaError_t setup(Scratch &sc) override {
+    const size_t blk = (size_t)M->n * mp;
+    cudaError_t e = sc.get(&b, blk);
+    if (e == cudaSuccess) e = sc.get(&x, blk);
+    if (e == cudaSuccess) e = sc.get(&iters_tot, mp);
+    if (e == cudaSuccess) e = sc.get(&outer_cnt, mp);
+    if (e == cudaSuccess) e = sc.get(&steps, 1);
+    if (mixed()) {
+      ens_solve_opts oo = o;
+      oo.precond = ENS_PRECOND_NONE;
+      if (e == cudaSuccess) e = S.setup(sc, M, mp, oo, s, true);
+      if (e == cudaSuccess) e = I.setup(sc, M, mp, o, s);
+      if (e == cudaSuccess) e = sc.get(&r32, blk);
+      if (e == cudaSuccess) e = sc.get(&d32, blk);
+      if (e == cudaSuccess) e = I.upload_tol(itol);
+    } else {
+      if (e == cudaSuccess) e = S.setup(sc, M, mp, o, s);
+    }
+    if (e == cudaSuccess) e = S.upload_tol(tolv);
+    return e;
+  }
+
+  cudaError_t record(cudaStream_t cap) override {
+    const int64_t n = M->n;
+    const int cgrid = M->num_sms * 8;
+    k_pad<<<cgrid, 256, 0, cap>>>(n, m, mp, B, b);
+    if (!o.x0_zero) k_pad<<<cgrid, 256, 0, cap>>>(n, m, mp, X, x);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(iters_tot, 0, mp * sizeof(int32_t), cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(outer_cnt, 0, mp * sizeof(int32_t), cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(steps, 0, sizeof(int32_t), cap);
+    if (e == cudaSuccess) e = S.enqueue_start(b, x, o.x0_zero != 0, singular, cap);
+    if (e != cudaSuccess) return e;
+    if (!mixed()) {
+      if (o.max_iter > 0) {
+        cudaGraphConditionalHandle h{};
+        cudaGraph_t body = nullptr;
+        e = capture_while(cap, &h, &body);
+        if (e == cudaSuccess)
+          e = capture_into(body, [&](cudaStream_t c) {
+            cudaError_t ek = S.iteration(x, o.max_iter, c);
+            if (ek == cudaSuccess) {
+              k_loop_cond<<<1, 32, 0, c>>>(h, S.cs.it);
+              ek = cudaGetLastError();
+            }
+            return ek;
+          });
+      }
+    } else {
+      cudaGraphConditionalHandle ho{};
+      cudaGraph_t obody = nullptr;
+      e = capture_while(cap, &ho, &obody);
+      if (e == cudaSuccess)
+        e = capture_into(obody, [&](cudaStream_t c) {
+          cudaError_t ek = with_vl(S.vec, S.lanes, [&](auto Vc, auto Lc) {
+            constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+            k_to32<V, L><<<S.grid, kThreads, 0, c>>>((int32_t)n, mp, S.r, r32, S.cs);
+            return cudaGetLastError();
+          });
+          if (ek == cudaSuccess) ek = I.enqueue_start(r32, d32, true, 0, c);
+          if (ek == cudaSuccess && o.max_iter > 0) {
+            cudaGraphConditionalHandle hi{};
+            cudaGraph_t ibody = nullptr;
+            ek = capture_while(c, &hi, &ibody);
+            if (ek == cudaSuccess)
+              ek = capture_into(ibody, [&](cudaStream_t c2) {
+                cudaError_t ei = I.iteration(d32, o.max_iter, c2);
+                if (ei == cudaSuccess) {
+                  k_loop_cond<<<1, 32, 0, c2>>>(hi, I.cs.it);
+                  ei = cudaGetLastError();
+                }
+                return ei;
+              });
+            // the inner loop's condition starts at 1 when the graph is launched; re-arm it after the
+            // loop ends so that the next outer step runs its inner solve again
+            if (ek == cudaSuccess) {
+              k_set_cond<<<1, 32, 0, c>>>(hi, 1u);
+              ek = cudaGetLastError();
+            }
+          }
+          if (ek == cudaSuccess) {
+            k_accum<<<1, 64, 0, c>>>(mp, S.cs.state, I.cs.iters, iters_tot, outer_cnt);
+            ek = cudaGetLastError();
+          }
+          if (ek == cudaSuccess)
+            ek = with_vl(S.vec, S.lanes, [&](auto Vc, auto Lc) {
+              constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+              k_correct<V, L><<<S.grid, kThreads, 0, c>>>((int32_t)n, mp, x, d32, S.cs);
+              return cudaGetLastError();
+            });
+          if (ek == cudaSuccess) ek = S.outer_residual(b, x, c);
+          if (ek == cudaSuccess) {
+            k_outer_cond<<<1, 32, 0, c>>>(ho, mp, S.cs.state, steps, o.max_outer);
+            ek = cudaGetLastError();
+          }
+          return ek;
+        });
+    }
+    if (e == cudaSuccess) e = S.finish(b, x, singular, cap);
+    if (e == cudaSuccess) {
+      k_unpad<<<cgrid, 256, 0, cap>>>(n, m, mp, x, X);
+      e = cudaGetLastError();
+    }
+    return e;
+  }
+
+  cudaError_t fetch() override {
+    h_iters.assign(mp, 0);
+    h_status.assign(mp, 0);
+    h_state.assign(mp, 0);
+    h_outer.assign(mp, 0);
+    h_relres.assign(mp, 0.0);
+    cudaError_t e = cudaMemcpyAsync(h_status.data(), S.cs.status, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_state.data(), S.cs.state, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_relres.data(), S.cs.relres, mp * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_iters.data(), mixed() ? iters_tot : S.cs.iters, mp * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && mixed()) e = cudaMemcpyAsync(h_outer.data(), outer_cnt, mp * 4, cudaMemcpyDeviceToHost, s);
+    return e;
+  }
+
+  void write(ens_solve_stats *st) override {
+    if (!st) return;
+    for (int l = 0; l < m; ++l) {
+      const int32_t status = h_state[l] != ST_DONE ? (int32_t)ENS_COL_MAXITER : h_status[l];
+      if (st->iters) st->iters[l] = h_iters[l];
+      if (st->status) st->status[l] = status;
+      if (st->relres) st->relres[l] = h_relres[l];
+      if (st->outer) st->outer[l] = h_outer[l];
+    }
+  }
+};
+
+SysBase *make_system_split(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                           const ens_solve_opts &o, cudaStream_t s);
+SysBase *make_system_native(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                            const ens_solve_opts &o, cudaStream_t s);
 
 extern template struct Bicg<ArithF32>;
 extern template struct Bicg<ArithF64Split>;
