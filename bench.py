@@ -217,6 +217,61 @@ def solve_metrics(reps: int = 2):
     return out
 
 
+def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float = 120e9, slots: int = 4):
+    """Poisson stream of solve requests (grids 64^3..192^3, channel and cube operators, m drawn from
+    {1, 2, 4, 8, 16, 32}, FP32 inner + FP64 refinement to 1e-8, Chebyshev) through the continuous-
+    batching server under an HBM budget. The arrival rate is `load` times the capacity measured by a
+    saturated burst of the same requests. Latency = arrival to result on the host."""
+    import gen
+    from paper_1711_10622_gb300.serving import Request, Server, latency_summary
+
+    ops = gen.serving_operators()
+    reqs = gen.serving_requests(count, ops, seed)
+    # one 64-column RHS pool per operator; a request takes m consecutive columns from a seeded offset
+    pools = {name: gen.rhs_normal(op.n, 64, 10622 + 500 + k, zero_mean=True) for k, (name, op) in enumerate(sorted(ops.items()))}
+    rng = __import__("numpy").random.default_rng(seed + 2)
+
+    def make(name, m):
+        c0 = int(rng.integers(0, 64 - m + 1))
+        return Request(name, pools[name][:, c0 : c0 + m].copy(), 1e-8)
+
+    with Server(ops, budget_bytes=budget, slots=slots, max_cols=32) as srv:
+        burst_n = min(16, count)
+        burst = [srv.submit(make(n, m)) for n, m, _ in reqs[:burst_n]]
+        for r in burst:
+            r.done.wait()
+        span = max(r.end for r in burst) - min(r.arrival for r in burst)
+        cap_rps = burst_n / span
+        rate = load * cap_rps
+        arrivals = gen.poisson_arrivals(count, rate, seed)
+        pending = [make(n, m) for n, m, _ in reqs]
+        t0 = time.perf_counter()
+        for r, ta in zip(pending, arrivals):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            srv.submit(r)
+        for r in pending:
+            r.done.wait()
+        peak = srv.sched.peak_in_flight + srv.sched.resident
+    s = latency_summary(pending)
+    s.update(
+        {
+            "arrival_rate_per_s": rate,
+            "load_vs_measured_capacity": load,
+            "capacity_requests_per_s": cap_rps,
+            "budget_gb": budget / 1e9,
+            "peak_admitted_gb": peak / 1e9,
+            "slots": slots,
+            "grids": sorted(ops),
+            "tol": 1e-8,
+            "precision": "mixed",
+            "converged_all": all((r.stats is not None and (r.stats["status"] == 0).all()) for r in pending),
+        }
+    )
+    return s
+
+
 def run_reference(args):
     """The CPU oracle as it stands, on a bounded row sample of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -313,6 +368,7 @@ def main():
     ap.add_argument("--f64-mode", default="auto", choices=["auto", "native", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true", help="skip the solve-throughput section")
+    ap.add_argument("--serving-requests", type=int, default=48, help="requests of the serving stream (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--profile", action="store_true", help="launch-only mode for ncu captures")
     ap.add_argument("--profile-size", default="half", choices=["half", "full"])
@@ -454,6 +510,10 @@ def main():
     }
 
     solves = None if args.no_solves else solve_metrics()
+    serving = None if args.serving_requests <= 0 else serving_metrics(args.serving_requests)
+    from paper_1711_10622_gb300 import report
+
+    estimate = report.estimate_table(per_m_us, n, nnz)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -485,6 +545,8 @@ def main():
             "sweep": sweep,
             "e2e": e2e,
             "solves": solves,
+            "serving": serving,
+            "paper_estimate": estimate,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": K * len(M_SWEEP),

@@ -15,6 +15,9 @@ from .workloads import (
     rhs_uniform,
     rhs_normal,
     WORKLOADS,
+    serving_operators,
+    serving_requests,
+    poisson_arrivals,
 )
 
 __all__ = [
@@ -28,4 +31,7 @@ __all__ = [
     "rhs_uniform",
     "rhs_normal",
     "WORKLOADS",
+    "serving_operators",
+    "serving_requests",
+    "poisson_arrivals",
 ]

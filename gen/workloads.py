@@ -111,6 +111,34 @@ def rhs_normal(n: int, m: int, seed: int, zero_mean: bool = False) -> np.ndarray
     return np.ascontiguousarray(b)
 
 
+def serving_operators(sizes=(64, 96, 128, 192)):
+    """The serving workload's operators: for each N, the channel N^3 and the cube case N^3 with cubes
+    of N/8 cells (pitch N/4)."""
+    ops = {}
+    for N in sizes:
+        ops[f"channel{N}"] = channel(N, N, N)
+        ops[f"cubes{N}"] = cubes(N, N, N, size=N // 8)
+    return ops
+
+
+def serving_requests(count, ops, seed=5, widths=(1, 2, 4, 8, 16, 32)):
+    """`count` requests (operator name, m, rhs seed), operator and m drawn uniformly from a seed."""
+    rng = np.random.default_rng(seed)
+    names = sorted(ops)
+    out = []
+    for k in range(count):
+        name = names[int(rng.integers(len(names)))]
+        m = int(widths[int(rng.integers(len(widths)))])
+        out.append((name, m, RHS_SEED_BASE + 1000 + k))
+    return out
+
+
+def poisson_arrivals(count, rate, seed=5):
+    """Arrival times (seconds from 0) of a Poisson process with the given rate."""
+    rng = np.random.default_rng(seed + 1)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
 # name -> (operator builder, m values, rhs builder(n, m)). The seeds are 10622 + workload id.
 WORKLOADS = {
     "dirichlet32_m4": dict(

@@ -42,7 +42,8 @@ typedef enum {
 typedef enum {
   ENS_COL_CONVERGED = 0,   /* ||b - A x||_2 / ||b||_2 <= tol (b = 0 gives x = 0, 0 iterations) */
   ENS_COL_MAXITER = 1,     /* iteration limit reached */
-  ENS_COL_BREAKDOWN = 2,   /* BiCGStab breakdown: rho ~ 0, (rhat, v) = 0 or (t, t) = 0 */
+  ENS_COL_BREAKDOWN = 2,   /* BiCGStab breakdown: rho ~ 0, (rhat, v) = 0, (t, t) = 0, omega = 0 or a
+                              non-finite step length (x keeps its last finite iterate) */
   ENS_COL_NONFINITE = 3,   /* NaN/Inf met in b, x0 or the iteration */
   ENS_COL_INCOMPATIBLE = 4 /* singular operator and sum(b) != 0 */
 } ens_col_status;
@@ -127,7 +128,7 @@ typedef enum { ENS_PRECOND_NONE = 0, ENS_PRECOND_CHEBYSHEV = 1 } ens_precond;
 typedef enum { ENS_PREC_F64 = 0, ENS_PREC_MIXED = 1 } ens_precision;
 
 typedef struct {
-  int32_t max_iter;    /* BiCGStab iterations per column (per inner solve in mixed mode); default 10000 */
+  int32_t max_iter;    /* BiCGStab iterations per column (FP64 mode); default 10000 */
   int32_t precond;     /* ENS_PRECOND_NONE (default) or ENS_PRECOND_CHEBYSHEV */
   int32_t cheb_steps;  /* Chebyshev updates per application, >= 1 (default 4 = 3 GSpMVs; polynomial
                           of degree cheb_steps - 1 in D^-1 A) */
@@ -137,6 +138,8 @@ typedef struct {
                           reductions, FP64 outer residual r = b - A x and correction x += d */
   double inner_tol;    /* mixed: relative residual of each FP32 inner solve (default 1e-4) */
   int32_t max_outer;   /* mixed: refinement steps (default 30) */
+  int32_t inner_max_iter; /* mixed: BiCGStab iterations per inner solve (default 1000); a stagnating
+                             inner solve is cut short and the next refinement step restarts it */
   int32_t check_every; /* host-driven loop only: iterations between reads of the convergence flags
                           (default 1) */
   int32_t x0_zero;     /* nonzero: ignore X on input and start from x0 = 0 */

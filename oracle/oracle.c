@@ -133,7 +133,8 @@ static int all_finite(int64_t n, const double *a) {
  * Right preconditioning x = M^-1 u. Stops when ||r||_2 / ||b||_2 <= tol (checked after the
  * half step on s and after the full step on r). Returns the per-column status; *iters is the
  * number of iterations begun; *relres the TRUE relative residual ||b - A x|| / ||b|| at exit.
- * Breakdown: |rho| <= 1e-300 * ||rhat|| ||r||, (rhat, v) == 0 or (t, t) == 0.
+ * Breakdown: |rho| <= 1e-300 * ||rhat|| ||r||, (rhat, v) == 0, (t, t) == 0, omega == 0, or a
+ * non-finite alpha or omega (detected before x is updated, so x keeps its last finite iterate).
  */
 int oracle_bicgstab(int64_t n, const int32_t *row, const int32_t *col, const double *val,
                     const double *b, double *x, double tol, const oracle_opts *o, int *iters,
@@ -180,7 +181,8 @@ int oracle_bicgstab(int64_t n, const int32_t *row, const int32_t *col, const dou
     apply_prec(o, n, row, col, val, p, ph);
     oracle_spmv(n, row, col, val, ph, 1, v, 1);
     const double rhv = dot(n, rh, v);
-    if (rhv == 0.0) { status = OR_BREAKDOWN; break; }
+    /* breakdown: (rhat, v) = 0, or a step length that is not finite (x keeps its last iterate) */
+    if (rhv == 0.0 || !isfinite(rho / rhv)) { status = OR_BREAKDOWN; break; }
     alpha = rho / rhv;
     for (int64_t i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
     if (sqrt(dot(n, s, s)) / bnorm <= tol) {
@@ -191,7 +193,7 @@ int oracle_bicgstab(int64_t n, const int32_t *row, const int32_t *col, const dou
     apply_prec(o, n, row, col, val, s, sh);
     oracle_spmv(n, row, col, val, sh, 1, t, 1);
     const double tt = dot(n, t, t);
-    if (tt == 0.0) { status = OR_BREAKDOWN; break; }
+    if (tt == 0.0 || !isfinite(dot(n, t, s) / tt)) { status = OR_BREAKDOWN; break; }
     omega = dot(n, t, s) / tt;
     for (int64_t i = 0; i < n; ++i) {
       x[i] = x[i] + alpha * ph[i] + omega * sh[i];

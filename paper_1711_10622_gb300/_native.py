@@ -48,6 +48,7 @@ class SolveOpts(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int32),
+        ("inner_max_iter", ctypes.c_int32),
         ("check_every", ctypes.c_int32),
         ("x0_zero", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),

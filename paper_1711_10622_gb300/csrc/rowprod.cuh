@@ -396,6 +396,24 @@ struct TileSmem {
   V va[kTileNnz];
 };
 
+// Visits the (row, column chunk) pairs of this thread in exactly the order tile_rows does, without
+// any product: kernels that skip the GSpMV (a zero initial guess) reduce in the same order as the
+// kernels that perform it, so both give the same bits.
+template <int VEC, int LANES, typename Fn>
+__device__ __forceinline__ void tile_order_rows(int64_t n, int32_t m, Fn &&fn) {
+  constexpr int G = 256 / LANES;
+  constexpr int RPG = kTileRows / G;
+  const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES;
+  for (int64_t r0 = (int64_t)blockIdx.x * kTileRows; r0 < n; r0 += (int64_t)gridDim.x * kTileRows) {
+    const int rows = (int)min((int64_t)kTileRows, n - r0);
+    for (int rr = 0; rr < RPG; ++rr) {
+      const int lr = rr * G + grp;
+      if (lr >= rows) break;
+      for (int32_t c = lane * VEC; c < m; c += LANES * VEC) fn(r0 + lr, c);
+    }
+  }
+}
+
 template <typename E>
 __device__ __forceinline__ void stage16(E *dst, const E *__restrict__ src, int32_t count) {
   // count elements, count * sizeof(E) a multiple of 16, src and dst 16-byte aligned

@@ -46,8 +46,8 @@ ens_status validate_solve(const ens_matrix *A, int32_t m, const double *B, doubl
   }
   if (o.precision != ENS_PREC_F64 && o.precision != ENS_PREC_MIXED)
     return fail(ENS_ERR_INVALID, "solve_block: unknown precision %d", o.precision);
-  if (o.precision == ENS_PREC_MIXED && (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0) || o.max_outer < 1))
-    return fail(ENS_ERR_INVALID, "solve_block: mixed mode needs 0 < inner_tol < 1 and max_outer >= 1");
+  if (o.precision == ENS_PREC_MIXED && (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0) || o.max_outer < 1 || o.inner_max_iter < 0))
+    return fail(ENS_ERR_INVALID, "solve_block: mixed mode needs 0 < inner_tol < 1, max_outer >= 1, inner_max_iter >= 0");
   if (o.check_every < 1) return fail(ENS_ERR_INVALID, "solve_block: check_every < 1");
   return ENS_OK;
 }
@@ -68,6 +68,7 @@ void ens_default_solve_opts(ens_solve_opts *o) {
   o->precision = ENS_PREC_F64;
   o->inner_tol = 1e-4;
   o->max_outer = 30;
+  o->inner_max_iter = 1000;
   o->check_every = 1;
   o->x0_zero = 0;
   o->use_graph = 1;

@@ -94,15 +94,13 @@ __global__ void __launch_bounds__(kThreads)
     if (rh) store_vec<T, VEC>(rh + i * m + cc, rv);
   };
   if (x0_zero) {
-    if (c < m) {
-      ENS_ROWS(i) {
-        T ax[VEC];
+    tile_order_rows<VEC, LANES>(A.n, m, [&](int64_t i, int32_t cc) {
+      T ax[VEC];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) ax[q] = T(0);
-        store_vec<T, VEC>(x + i * m + c, ax);
-        fin_row(i, c, ax);
-      }
-    }
+      for (int q = 0; q < VEC; ++q) ax[q] = T(0);
+      store_vec<T, VEC>(x + i * m + cc, ax);
+      fin_row(i, cc, ax);
+    });
   } else {
     tile_rows<Arith, VEC, LANES>(A, m, x, mask, fin_row);
   }
@@ -239,12 +237,13 @@ __global__ void __launch_bounds__(kThreads)
     if (cs.state[l] != ST_ACTIVE) return;
     cs.iters[l] = cs.it[0] + 1;
     const T rv = t.v[0][l];
-    if (rv == T(0)) {
+    const T al = cs.rho[l] / rv;
+    if (rv == T(0) || !isfinite(al)) {  // breakdown; x keeps its last finite iterate
       cs.state[l] = ST_DONE;
       cs.status[l] = ENS_COL_BREAKDOWN;
       return;
     }
-    cs.alpha[l] = cs.rho[l] / rv;
+    cs.alpha[l] = al;
   });
 }
 
@@ -310,12 +309,13 @@ __global__ void __launch_bounds__(kThreads)
   reduce_cols<T, 2, VEC, LANES>(acc, m, partials, counter, [&](int l, const ColTotals<T, 2> &tt) {
     if (cs.state[l] != ST_ACTIVE) return;
     const T t2 = tt.v[1][l];
-    if (t2 == T(0)) {
+    const T om = tt.v[0][l] / t2;
+    if (t2 == T(0) || !isfinite(om)) {  // breakdown before x is updated with a non-finite step
       cs.state[l] = ST_DONE;
       cs.status[l] = ENS_COL_BREAKDOWN;
       return;
     }
-    cs.omega[l] = tt.v[0][l] / t2;
+    cs.omega[l] = om;
   });
 }
 
@@ -519,12 +519,14 @@ __global__ void __launch_bounds__(kThreads)
 // x += ||r|| d for active outer columns (the FP64 correction step).
 template <int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
-    k_correct(int32_t n, int32_t m, double *x, const float *__restrict__ d, Cols<double> cs) {
+    k_correct(int32_t n, int32_t m, double *x, const float *__restrict__ d, Cols<double> cs,
+              const int32_t *__restrict__ inner_status) {
   const int32_t c = (threadIdx.x % LANES) * VEC;
   if (c >= m) return;
   double sc[VEC];
 #pragma unroll
-  for (int q = 0; q < VEC; ++q) sc[q] = cs.state[c + q] == ST_ACTIVE ? sqrt(cs.rn2[c + q]) : 0.0;
+  for (int q = 0; q < VEC; ++q)  // an inner solve that met a non-finite value contributes nothing
+    sc[q] = cs.state[c + q] == ST_ACTIVE && inner_status[c + q] != ENS_COL_NONFINITE ? sqrt(cs.rn2[c + q]) : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < n;
        i += (int64_t)gridDim.x * (kThreads / LANES)) {
     double xv[VEC];
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(kThreads)
     load_vec_rw<double, VEC>(x + i * m + c, xv);
     load_vec<float, VEC>(d + i * m + c, dv);
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) xv[q] += sc[q] * (double)dv[q];
+    for (int q = 0; q < VEC; ++q) xv[q] = sc[q] != 0.0 ? xv[q] + sc[q] * (double)dv[q] : xv[q];
     store_vec<double, VEC>(x + i * m + c, xv);
   }
 }
@@ -913,7 +915,7 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
       });
       if (e == cudaSuccess) e = I.start(r32, d32, true, 0, itol);
       int ran = 0;
-      if (e == cudaSuccess) e = I.iterate(d32, o.max_iter, o.check_every, o.use_graph != 0, &ran);
+      if (e == cudaSuccess) e = I.iterate(d32, o.inner_max_iter, o.check_every, o.use_graph != 0, &ran);
       if (e == cudaSuccess) e = cudaMemcpyAsync(inner_it.data(), I.cs.iters, mp * 4, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) break;
@@ -924,7 +926,7 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
         }
       e = with_vl(O.vec, O.lanes, [&](auto Vc, auto Lc) {
         constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-        k_correct<V, L><<<O.grid, kThreads, 0, s>>>((int32_t)n, mp, x, d32, O.cs);
+        k_correct<V, L><<<O.grid, kThreads, 0, s>>>((int32_t)n, mp, x, d32, O.cs, I.cs.status);
         return cudaGetLastError();
       });
       if (e == cudaSuccess) e = O.outer_residual(b, x);
@@ -1126,13 +1128,13 @@ struct SysImpl : SysBase {
             return cudaGetLastError();
           });
           if (ek == cudaSuccess) ek = I.enqueue_start(r32, d32, true, 0, c);
-          if (ek == cudaSuccess && o.max_iter > 0) {
+          if (ek == cudaSuccess && o.inner_max_iter > 0) {
             cudaGraphConditionalHandle hi{};
             cudaGraph_t ibody = nullptr;
             ek = capture_while(c, &hi, &ibody);
             if (ek == cudaSuccess)
               ek = capture_into(ibody, [&](cudaStream_t c2) {
-                cudaError_t ei = I.iteration(d32, o.max_iter, c2);
+                cudaError_t ei = I.iteration(d32, o.inner_max_iter, c2);
                 if (ei == cudaSuccess) {
                   k_loop_cond<<<1, 32, 0, c2>>>(hi, I.cs.it);
                   ei = cudaGetLastError();
@@ -1153,7 +1155,7 @@ struct SysImpl : SysBase {
           if (ek == cudaSuccess)
             ek = with_vl(S.vec, S.lanes, [&](auto Vc, auto Lc) {
               constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-              k_correct<V, L><<<S.grid, kThreads, 0, c>>>((int32_t)n, mp, x, d32, S.cs);
+              k_correct<V, L><<<S.grid, kThreads, 0, c>>>((int32_t)n, mp, x, d32, S.cs, I.cs.status);
               return cudaGetLastError();
             });
           if (ek == cudaSuccess) ek = S.outer_residual(b, x, c);
