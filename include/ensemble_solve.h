@@ -122,6 +122,26 @@ ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *
  */
 ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream);
 
+/*
+ * ens_gspmv_host without device allocation. (The paper has no counterpart: this is a deployment
+ * variant of ens_gspmv_host.) For callers that cannot let a library allocate device memory during
+ * a call: applications that reserve all device memory for their own pool up front, real-time loops
+ * that cannot afford an allocation's latency or implicit synchronisation, and hosts that forbid
+ * plug-in libraries from allocating. It calls no cudaMalloc, cudaFree or other allocating routine:
+ * X and Y are staged through one array compiled into the library, 2 x 16 MiB, which every GPU that
+ * loads the library holds until the process exits.
+ *   Same arguments, semantics and accuracy as ens_gspmv_host (host X read, host Y written;
+ *   synchronous). n * m * sizeof(dtype) must not exceed 16 MiB (16,777,216 bytes; e.g. n*m <= 2,097,152
+ *   for float64); larger requests return ENS_ERR_INVALID. The matrix's device must be current.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *   device current; make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents; nothing in it needs to start at
+ *   zero (each call overwrites the staged X and all of Y). Calls whose GPU work overlapped would race
+ *   on it; this entry point serialises its callers with a lock and returns only after its own copies
+ *   finish, so calls made through it do not overlap within a process.
+ */
+ens_status ens_gspmv_host_noalloc(const ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream);
+
 /* ---------------------------------------------------------------- multi-RHS BiCGStab solve */
 
 typedef enum { ENS_PRECOND_NONE = 0, ENS_PRECOND_CHEBYSHEV = 1 } ens_precond;

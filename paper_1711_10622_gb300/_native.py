@@ -117,6 +117,7 @@ def lib():
         ),
         "ens_gspmv": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_gspmv_host": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+        "ens_gspmv_host_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),
         "ens_solve_block": (
             _i32,
