@@ -15,7 +15,10 @@
  *   - Errors: every call returns an ens_status; on failure nothing is enqueued and a message is
  *     available from ens_last_error() (per host thread). Sizes and pointers are validated on the
  *     host before any launch.
- *   - One ens_matrix may be used from one host thread at a time (its workspaces are shared).
+ *   - Threads: ens_gspmv, ens_solve_block and ens_solve_batch keep their scratch per call and may
+ *     run concurrently on one matrix from several host threads / streams. ens_gspmv_host,
+ *     ens_autotune, ens_set_f64_mode and ens_set_native_share change per-matrix state: call them
+ *     from one host thread at a time per matrix, not concurrently with other calls on it.
  */
 #ifndef ENSEMBLE_SOLVE_H
 #define ENSEMBLE_SOLVE_H
