@@ -242,7 +242,7 @@ def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float 
         burst_n = min(16, count)
         burst = [srv.submit(make(n, m)) for n, m, _ in reqs[:burst_n]]
         for r in burst:
-            r.done.wait()
+            r.done.wait(600)
         span = max(r.end for r in burst) - min(r.arrival for r in burst)
         cap_rps = burst_n / span
         rate = load * cap_rps
@@ -255,8 +255,10 @@ def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float 
                 time.sleep(dt)
             srv.submit(r)
         for r in pending:
-            r.done.wait()
+            r.done.wait(900)
         peak = srv.sched.peak_in_flight + srv.sched.resident
+        unfinished = sum(1 for r in pending if not r.done.is_set())
+        pending = [r for r in pending if r.done.is_set()]
     s = latency_summary(pending)
     s.update(
         {
@@ -270,6 +272,7 @@ def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float 
             "tol": 1e-8,
             "precision": "mixed",
             "converged_all": all((r.stats is not None and (r.stats["status"] == 0).all()) for r in pending),
+            "unfinished": unfinished,
         }
     )
     return s

@@ -60,8 +60,10 @@ typedef enum { ENS_F64 = 0, ENS_F32 = 1 } ens_dtype;
 typedef enum {
   ENS_F64_AUTO = 0,   /* library choice (split-float arithmetic where values allow) */
   ENS_F64_NATIVE = 1, /* native double-precision FMA for every product */
-  ENS_F64_SPLIT = 2   /* double-float products on the FP32 pipe, native FP64 fallback per row
+  ENS_F64_SPLIT = 2,  /* double-float products on the FP32 pipe, native FP64 fallback per row
                          segment whose values fall outside the split range */
+  ENS_F64_HYBRID = 3  /* per lane, one column with native DFMA and one with split-float arithmetic,
+                         so the FP64 and FP32/integer pipes work at once (even m; odd m: native) */
 } ens_f64_mode;
 
 /*
@@ -100,10 +102,11 @@ ens_status ens_set_native_share(ens_matrix *A, int32_t share);
 /*
  * Autotuner: time the GSpMV launch candidates for block width m (1..64) and dtype on this matrix
  * (lanes per row, i.e. rows per warp and column-tile width; for FP64 also native DFMA vs split-float
- * with native shares 0, 8, 16, 24 of 32) and keep the fastest for later ens_gspmv calls and for the
- * solver's products of that width. Uses temporary device blocks of n x m (stream-ordered, freed
- * before return). Synchronous. Optional outputs: chosen lanes, chosen share (32 = native), and the
- * best time per launch in microseconds. A share set with ens_set_native_share still takes priority.
+ * with native shares 0, 8, 16, 24 of 32, and the column hybrid) and keep the fastest for later
+ * ens_gspmv calls and for the solver's products of that width. Uses temporary device blocks of
+ * n x m (stream-ordered, freed before return). Synchronous. Optional outputs: chosen lanes, chosen
+ * share (32 = native, 64 = column hybrid), and the best time per launch in microseconds. A share
+ * set with ens_set_native_share, or ENS_F64_HYBRID / ENS_F64_SPLIT modes, still take priority.
  */
 ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, int32_t *lanes, int32_t *share,
                         double *best_us);
@@ -159,9 +162,11 @@ typedef struct {
   double cheb_hi;      /* (default [2/30, 2]; 2 bounds D^-1 A of diagonally dominant M-matrices) */
   int32_t precision;   /* ENS_PREC_F64 (default) or ENS_PREC_MIXED: FP32 inner BiCGStab with FP32
                           reductions, FP64 outer residual r = b - A x and correction x += d */
-  double inner_tol;    /* mixed: relative residual of each FP32 inner solve (default 1e-4) */
-  int32_t max_outer;   /* mixed: refinement steps (default 30) */
-  int32_t inner_max_iter; /* mixed: BiCGStab iterations per inner solve (default 1000); a stagnating
+  double inner_tol;    /* mixed: relative residual of each FP32 inner solve (default 1e-3; FP32
+                          cannot resolve much below cond(A) * 6e-8, and each refinement step only
+                          needs a reliable reduction) */
+  int32_t max_outer;   /* mixed: refinement steps (default 50) */
+  int32_t inner_max_iter; /* mixed: BiCGStab iterations per inner solve (default 100); a stagnating
                              inner solve is cut short and the next refinement step restarts it */
   int32_t check_every; /* host-driven loop only: iterations between reads of the convergence flags
                           (default 1) */

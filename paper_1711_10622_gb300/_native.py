@@ -23,7 +23,7 @@ STATUS_NAMES = {
 }
 ENS_F64, ENS_F32 = 0, 1
 ENS_MATRIX_SINGULAR = 0x1
-ENS_F64_AUTO, ENS_F64_NATIVE, ENS_F64_SPLIT = 0, 1, 2
+ENS_F64_AUTO, ENS_F64_NATIVE, ENS_F64_SPLIT, ENS_F64_HYBRID = 0, 1, 2, 3
 COL_CONVERGED, COL_MAXITER, COL_BREAKDOWN, COL_NONFINITE, COL_INCOMPATIBLE = range(5)
 
 _vp = ctypes.c_void_p

@@ -79,7 +79,7 @@ class Matrix:
         return self._h
 
     def set_f64_mode(self, mode: str):
-        code = {"auto": N.ENS_F64_AUTO, "native": N.ENS_F64_NATIVE, "split": N.ENS_F64_SPLIT}[mode]
+        code = {"auto": N.ENS_F64_AUTO, "native": N.ENS_F64_NATIVE, "split": N.ENS_F64_SPLIT, "hybrid": N.ENS_F64_HYBRID}[mode]
         N.check(N.lib().ens_set_f64_mode(self.handle, code))
 
     def set_native_share(self, share: int):

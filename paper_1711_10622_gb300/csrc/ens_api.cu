@@ -199,7 +199,7 @@ ens_status ens_matrix_info(const ens_matrix *A, int64_t *n, int64_t *nnz, int32_
 ens_status ens_set_f64_mode(ens_matrix *A, int32_t mode) {
   clear_error();
   if (!A) return fail(ENS_ERR_INVALID, "set_f64_mode: matrix is NULL");
-  if (mode < ENS_F64_AUTO || mode > ENS_F64_SPLIT) return fail(ENS_ERR_INVALID, "set_f64_mode: unknown mode %d", mode);
+  if (mode < ENS_F64_AUTO || mode > ENS_F64_HYBRID) return fail(ENS_ERR_INVALID, "set_f64_mode: unknown mode %d", mode);
   A->f64_mode = mode;
   return ENS_OK;
 }

@@ -9,6 +9,7 @@
 #include "ensemble_solve.h"
 
 constexpr int kTuneMaxM = 64;  // block widths the autotuner keeps a choice for
+constexpr int kShareHybrid = 64;  // "native share" code of the column-hybrid FP64 arithmetic
 
 struct ens_matrix {
   int64_t n = 0, nnz = 0;

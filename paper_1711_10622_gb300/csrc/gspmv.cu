@@ -89,6 +89,7 @@ bool use_split(const ens_matrix *A) {
 // pipe is otherwise idle, so hybrid tiles add its throughput to that of the split path. A value
 // set with ens_set_native_share overrides the table.
 int native_share(const ens_matrix *A, int m) {
+  if (A->f64_mode == ENS_F64_HYBRID) return kShareHybrid;
   if (A->native_share >= 0) return A->native_share;
   if (A->f64_mode == ENS_F64_SPLIT) return 0;
   if (m >= 1 && m <= kTuneMaxM && A->tuned_share[m] >= 0) return A->tuned_share[m];
@@ -148,6 +149,10 @@ cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, voi
     if (c.vec == 4) return dispatch<ArithF32, 4>(A, m, X, Y, c.lanes, 0u, s);
     if (c.vec == 2) return dispatch<ArithF32, 2>(A, m, X, Y, c.lanes, 0u, s);
     return dispatch<ArithF32, 1>(A, m, X, Y, c.lanes, 0u, s);
+  }
+  if (c.share == kShareHybrid) {  // column hybrid needs two columns per lane
+    return c.vec == 2 ? dispatch<ArithF64Hybrid, 2>(A, m, X, Y, c.lanes, 0u, s)
+                      : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, s);
   }
   if (c.share < 32) {
     const uint32_t mask = share_mask(c.share);
@@ -211,8 +216,10 @@ ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *la
       cand.push_back(Cfg{base.vec, lanes, 0});
     } else {
       cand.push_back(Cfg{base.vec, lanes, 32});
-      if (use_split(A))
+      if (use_split(A)) {
         for (int sh : {0, 8, 16, 24}) cand.push_back(Cfg{base.vec, lanes, sh});
+        if (base.vec == 2) cand.push_back(Cfg{base.vec, lanes, kShareHybrid});
+      }
     }
   }
   cudaEvent_t t0 = nullptr, t1 = nullptr;

@@ -35,7 +35,7 @@ template <typename T, int ND, int VEC, int LANES, typename Fin, typename After =
 __device__ __forceinline__ void reduce_cols(T (&acc)[ND][VEC], int32_t m, T *__restrict__ partials,
                                             unsigned *__restrict__ counter, Fin &&fin, After &&after = After()) {
   constexpr int kWarps = kThreads / 32;
-  __shared__ T sm[kWarps][ND][kMaxSolveM];
+  __shared__ ColTotals<T, ND> blk;  // block sums, accumulated warp by warp in a fixed order
   __shared__ ColTotals<T, ND> tot;
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -45,23 +45,19 @@ __device__ __forceinline__ void reduce_cols(T (&acc)[ND][VEC], int32_t m, T *__r
     for (int d = 0; d < ND; ++d)
 #pragma unroll
       for (int q = 0; q < VEC; ++q) acc[d][q] += __shfl_xor_sync(0xffffffffu, acc[d][q], off);
-  if (lane < LANES) {
+  for (int w = 0; w < kWarps; ++w) {
+    if (warp == w && lane < LANES) {
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) {
-      const int c = lane * VEC + q;
-      if (c < m)
+      for (int q = 0; q < VEC; ++q) {
+        const int c = lane * VEC + q;
+        if (c < m)
 #pragma unroll
-        for (int d = 0; d < ND; ++d) sm[warp][d][c] = acc[d][q];
+          for (int d = 0; d < ND; ++d) blk.v[d][c] = w == 0 ? acc[d][q] : blk.v[d][c] + acc[d][q];
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < ND * m; t += kThreads) {
-    const int d = t / m, c = t % m;
-    T s = sm[0][d][c];
-#pragma unroll
-    for (int w = 1; w < kWarps; ++w) s += sm[w][d][c];
-    partials[(size_t)blockIdx.x * ND * m + t] = s;
-  }
+  for (int t = threadIdx.x; t < ND * m; t += kThreads) partials[(size_t)blockIdx.x * ND * m + t] = blk.v[t / m][t % m];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;

@@ -336,55 +336,7 @@ __device__ __forceinline__ void row_split<2>(int32_t j0, int32_t j1, const int32
   }
 }
 
-// Arithmetic selectors. V is the per-nonzero value type staged in shared memory; row() computes
-// one row segment from CSR arrays indexed by [j0, j1) (shared tile or global), vn being the
-// float64 values under the same index; native forces DFMA (hybrid split/native tiles).
-struct ArithF32 {
-  using T = float;
-  using V = float;
-  __device__ __forceinline__ static const V *vals(const MatView &A) { return A.val32; }
-  template <int VEC>
-  __device__ __forceinline__ static void row(const int32_t *ci, const V *va, const double *, int32_t j0, int32_t j1,
-                                             int32_t m, int32_t c, const float *X, float (&y)[VEC], bool) {
-    row_plain<float, float, VEC>(j0, j1, ci, va, m, c, X, y);
-  }
-  __device__ __forceinline__ static float dinv(const MatView &A, int64_t i) { return __ldg(A.dinv32 + i); }
-};
-struct ArithF64Native {
-  using T = double;
-  using V = double;
-  __device__ __forceinline__ static const V *vals(const MatView &A) { return A.val; }
-  template <int VEC>
-  __device__ __forceinline__ static void row(const int32_t *ci, const V *va, const double *, int32_t j0, int32_t j1,
-                                             int32_t m, int32_t c, const double *X, double (&y)[VEC], bool) {
-    row_plain<double, double, VEC>(j0, j1, ci, va, m, c, X, y);
-  }
-  __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
-};
-struct ArithF64Split {
-  using T = double;
-  using V = float2;
-  __device__ __forceinline__ static const V *vals(const MatView &A) { return A.vs; }
-  template <int VEC>
-  __device__ __forceinline__ static void row(const int32_t *ci, const V *va, const double *vn, int32_t j0, int32_t j1,
-                                             int32_t m, int32_t c, const double *X, double (&y)[VEC], bool native) {
-    if (native)
-      row_native_f64<VEC>(j0, j1, ci, vn, m, c, X, y);
-    else
-      row_split<VEC>(j0, j1, ci, va, vn, m, c, X, y);
-  }
-  __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
-};
-
-// ------------------------------------------------------------------ row tiles
-// A block walks tiles of kTileRows consecutive rows (grid-stride). For each tile it stages the
-// row pointers and the tile's contiguous CSR segment (column indices and values) in shared
-// memory with 16-byte coalesced loads (the arrays are padded so the rounded-out segment stays
-// inside them), then each row group of LANES threads computes rows g, g + G, g + 2G, ... of the
-// tile from shared memory and hands each (row, column chunk) result to the epilogue. A tile
-// whose segment exceeds kTileNnz is computed from global memory instead. native_mask bit
-// (s & 31) sends row sweep s (counted over all tiles) to native DFMA (split arithmetic only), so the
-// FP64 pipe takes a share of the products while the FP32/integer pipes take the rest.
+// ------------------------------------------------------------------ row tiles (shared memory)
 constexpr int kTileRows = 256;
 constexpr int kTileNnz = 2048;
 constexpr int kCsrPad = 4;  // extra elements allocated after row_ptr, col_idx and every value array
@@ -395,6 +347,191 @@ struct TileSmem {
   int32_t ci[kTileNnz];
   V va[kTileNnz];
 };
+
+template <typename E>
+__device__ __forceinline__ void stage16(E *dst, const E *__restrict__ src, int32_t count) {
+  // count elements, count * sizeof(E) a multiple of 16, src and dst 16-byte aligned
+  const int32_t n16 = count * (int32_t)sizeof(E) / 16;
+  const int4 *s = reinterpret_cast<const int4 *>(src);
+  int4 *d = reinterpret_cast<int4 *>(dst);
+  for (int32_t t = threadIdx.x; t < n16; t += blockDim.x) d[t] = __ldcs(s + t);
+}
+
+// ------------------------------------------------------------------ column-hybrid float64
+// Each lane owns two columns: the first is computed with native DFMA, the second with split-float
+// arithmetic, in the same instruction stream. The FP64 pipe and the FP32/integer pipes then work
+// at the same time on every warp instead of taking turns. Column 1 falls back to DFMA when its X
+// values leave the split range (decided for that column alone).
+template <int VEC>
+__device__ __forceinline__ void row_hybrid(int32_t j0, int32_t j1, const int32_t *ci, const double *vd,
+                                           const float2 *vs, int32_t m, int32_t c, const double *__restrict__ X,
+                                           double (&y)[VEC]);
+template <>
+__device__ __forceinline__ void row_hybrid<2>(int32_t j0, int32_t j1, const int32_t *ci, const double *vd,
+                                              const float2 *vs, int32_t m, int32_t c, const double *__restrict__ X,
+                                              double (&y)[2]) {
+  double acc = 0.0;
+  float sh = 0.f, sl = 0.f;
+  bool ok = true;
+  int32_t j = j0;
+  for (; j + kUnroll <= j1; j += kUnroll) {
+    int32_t k[kUnroll];
+    double ad[kUnroll];
+    float2 as[kUnroll];
+    double x[kUnroll][2];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      k[u] = ci[j + u];
+      ad[u] = vd[j + u];
+      as[u] = vs[j + u];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) load_vec<double, 2>(X + (int64_t)k[u] * m + c, x[u]);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      acc = fma(ad[u], x[u][0], acc);
+      float xh, xl;
+      ok &= split_f64(x[u][1], xh, xl);
+      split_fma(as[u].x, as[u].y, xh, xl, sh, sl);
+    }
+  }
+  for (; j < j1; ++j) {
+    double x[2];
+    load_vec<double, 2>(X + (int64_t)ci[j] * m + c, x);
+    acc = fma(vd[j], x[0], acc);
+    float xh, xl;
+    ok &= split_f64(x[1], xh, xl);
+    split_fma(vs[j].x, vs[j].y, xh, xl, sh, sl);
+  }
+  y[0] = acc;
+  y[1] = split_to_double(sh, sl);
+  if (!ok) {
+    double z = 0.0;
+    for (int32_t jj = j0; jj < j1; ++jj) z = fma(vd[jj], __ldg(X + (int64_t)ci[jj] * m + c + 1), z);
+    y[1] = z;
+  }
+}
+template <>
+__device__ __forceinline__ void row_hybrid<1>(int32_t j0, int32_t j1, const int32_t *ci, const double *vd,
+                                              const float2 *, int32_t m, int32_t c, const double *__restrict__ X,
+                                              double (&y)[1]) {
+  row_plain<double, double, 1>(j0, j1, ci, vd, m, c, X, y);
+}
+
+// ------------------------------------------------------------------ arithmetic policies
+// T: element type of X and Y. Tile: the shared-memory layout of a staged row tile. stage() copies
+// the tile's CSR segment [ab, ae) (16-byte rounded) into it; row_s() computes one row segment
+// from the tile, row_g() from global memory (tiles whose segment does not fit). `native` forces
+// DFMA for the sweep (split arithmetic with a native share).
+struct ArithF32 {
+  using T = float;
+  using Tile = TileSmem<float>;
+  __device__ __forceinline__ static void stage(Tile &sm, const MatView &A, int32_t ab, int32_t ae) {
+    stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
+    stage16<float>(sm.va, A.val32 + ab, ae - ab);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_s(const Tile &sm, const MatView &, int32_t, int32_t j0, int32_t j1,
+                                               int32_t m, int32_t c, const float *X, float (&y)[VEC], bool) {
+    row_plain<float, float, VEC>(j0, j1, sm.ci, sm.va, m, c, X, y);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_g(const MatView &A, int32_t ab, int32_t j0, int32_t j1, int32_t m,
+                                               int32_t c, const float *X, float (&y)[VEC], bool) {
+    row_plain<float, float, VEC>(j0, j1, A.ci + ab, A.val32 + ab, m, c, X, y);
+  }
+  __device__ __forceinline__ static float dinv(const MatView &A, int64_t i) { return __ldg(A.dinv32 + i); }
+};
+struct ArithF64Native {
+  using T = double;
+  using Tile = TileSmem<double>;
+  __device__ __forceinline__ static void stage(Tile &sm, const MatView &A, int32_t ab, int32_t ae) {
+    stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
+    stage16<double>(sm.va, A.val + ab, ae - ab);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_s(const Tile &sm, const MatView &, int32_t, int32_t j0, int32_t j1,
+                                               int32_t m, int32_t c, const double *X, double (&y)[VEC], bool) {
+    row_plain<double, double, VEC>(j0, j1, sm.ci, sm.va, m, c, X, y);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_g(const MatView &A, int32_t ab, int32_t j0, int32_t j1, int32_t m,
+                                               int32_t c, const double *X, double (&y)[VEC], bool) {
+    row_plain<double, double, VEC>(j0, j1, A.ci + ab, A.val + ab, m, c, X, y);
+  }
+  __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
+};
+struct ArithF64Split {
+  using T = double;
+  using Tile = TileSmem<float2>;
+  __device__ __forceinline__ static void stage(Tile &sm, const MatView &A, int32_t ab, int32_t ae) {
+    stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
+    stage16<float2>(sm.va, A.vs + ab, ae - ab);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_s(const Tile &sm, const MatView &A, int32_t ab, int32_t j0, int32_t j1,
+                                               int32_t m, int32_t c, const double *X, double (&y)[VEC], bool native) {
+    if (native)
+      row_native_f64<VEC>(j0, j1, sm.ci, A.val + ab, m, c, X, y);
+    else
+      row_split<VEC>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_g(const MatView &A, int32_t ab, int32_t j0, int32_t j1, int32_t m,
+                                               int32_t c, const double *X, double (&y)[VEC], bool native) {
+    if (native)
+      row_native_f64<VEC>(j0, j1, A.ci + ab, A.val + ab, m, c, X, y);
+    else
+      row_split<VEC>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
+  }
+  __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
+};
+// Column hybrid: the tile holds the float64 values and their (hi, lo) split, computed once per
+// staged value (amortised over all lanes of the tile); only the float64 array is read from HBM.
+struct HybridTile {
+  int32_t rp[kTileRows + 4];
+  int32_t ci[kTileNnz];
+  double vd[kTileNnz];
+  float2 vs[kTileNnz];
+};
+struct ArithF64Hybrid {
+  using T = double;
+  using Tile = HybridTile;
+  __device__ __forceinline__ static void stage(Tile &sm, const MatView &A, int32_t ab, int32_t ae) {
+    stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
+    const int32_t n16 = (ae - ab) / 2;  // two doubles per 16 bytes
+    const int4 *src = reinterpret_cast<const int4 *>(A.val + ab);
+    for (int32_t t = threadIdx.x; t < n16; t += blockDim.x) {
+      const int4 q = __ldcs(src + t);
+      reinterpret_cast<int4 *>(sm.vd)[t] = q;
+      const double v0 = __hiloint2double(q.y, q.x), v1 = __hiloint2double(q.w, q.z);
+      float h0, l0, h1, l1;
+      split_f64(v0, h0, l0);  // matrix values are inside the split range (checked at creation)
+      split_f64(v1, h1, l1);
+      reinterpret_cast<float4 *>(sm.vs)[t] = make_float4(h0, l0, h1, l1);
+    }
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_s(const Tile &sm, const MatView &, int32_t, int32_t j0, int32_t j1,
+                                               int32_t m, int32_t c, const double *X, double (&y)[VEC], bool) {
+    row_hybrid<VEC>(j0, j1, sm.ci, sm.vd, sm.vs, m, c, X, y);
+  }
+  template <int VEC>
+  __device__ __forceinline__ static void row_g(const MatView &A, int32_t ab, int32_t j0, int32_t j1, int32_t m,
+                                               int32_t c, const double *X, double (&y)[VEC], bool) {
+    row_native_f64<VEC>(j0, j1, A.ci + ab, A.val + ab, m, c, X, y);
+  }
+  __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
+};
+
+// A block walks tiles of kTileRows consecutive rows (grid-stride). For each tile it stages the
+// row pointers and the tile's contiguous CSR segment (column indices and values) in shared
+// memory with 16-byte coalesced loads (the arrays are padded so the rounded-out segment stays
+// inside them), then each row group of LANES threads computes rows g, g + G, g + 2G, ... of the
+// tile from shared memory and hands each (row, column chunk) result to the epilogue. A tile
+// whose segment exceeds kTileNnz is computed from global memory instead. native_mask bit
+// (s & 31) sends row sweep s (counted over all tiles) to native DFMA (split arithmetic only), so the
+// FP64 pipe takes a share of the products while the FP32/integer pipes take the rest.
 
 // Visits the (row, column chunk) pairs of this thread in exactly the order tile_rows does, without
 // any product: kernels that skip the GSpMV (a zero initial guess) reduce in the same order as the
@@ -414,38 +551,23 @@ __device__ __forceinline__ void tile_order_rows(int64_t n, int32_t m, Fn &&fn) {
   }
 }
 
-template <typename E>
-__device__ __forceinline__ void stage16(E *dst, const E *__restrict__ src, int32_t count) {
-  // count elements, count * sizeof(E) a multiple of 16, src and dst 16-byte aligned
-  const int32_t n16 = count * (int32_t)sizeof(E) / 16;
-  const int4 *s = reinterpret_cast<const int4 *>(src);
-  int4 *d = reinterpret_cast<int4 *>(dst);
-  for (int32_t t = threadIdx.x; t < n16; t += blockDim.x) d[t] = __ldcs(s + t);
-}
-
 template <typename Arith, int VEC, int LANES, typename Epi>
 __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typename Arith::T *__restrict__ X,
                                           uint32_t native_mask, Epi &&epi) {
   using T = typename Arith::T;
-  using V = typename Arith::V;
   constexpr int kThr = 256;
   constexpr int G = kThr / LANES;
   constexpr int RPG = kTileRows / G;
-  __shared__ __align__(16) TileSmem<V> sm;
+  __shared__ __align__(16) typename Arith::Tile sm;
   const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES;
-  const V *gva = Arith::vals(A);
   for (int64_t r0 = (int64_t)blockIdx.x * kTileRows; r0 < A.n; r0 += (int64_t)gridDim.x * kTileRows) {
     const int rows = (int)min((int64_t)kTileRows, (int64_t)A.n - r0);
     stage16<int32_t>(sm.rp, A.rp + r0, (rows + 1 + 3) & ~3);
     __syncthreads();
     const int32_t ab = sm.rp[0] & ~3, ae = (sm.rp[rows] + 3) & ~3;
     const bool staged = ae - ab <= kTileNnz;
-    if (staged) {
-      stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
-      stage16<V>(sm.va, gva + ab, ae - ab);
-    }
+    if (staged) Arith::stage(sm, A, ab, ae);
     __syncthreads();
-    const double *vn = A.val + ab;
     // sweep counter: spreads native_mask over tiles; the per-warp rotation keeps warps of one SM in
     // different phases so the FP64 pipe (native sweeps) and the FP32/integer pipes (split sweeps)
     // work at the same time
@@ -459,13 +581,11 @@ __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typ
         const bool nat = (native_mask >> ((sweep0 + rr) & 31)) & 1u;
         for (int32_t c = lane * VEC; c < m; c += LANES * VEC) {
           T y[VEC];
-          Arith::template row<VEC>(sm.ci, sm.va, vn, j0, j1, m, c, X, y, nat);
+          Arith::template row_s<VEC>(sm, A, ab, j0, j1, m, c, X, y, nat);
           epi(r0 + lr, c, y);
         }
       }
     } else {
-      const int32_t *gci = A.ci + ab;
-      const V *gv = gva + ab;
 #pragma unroll 1
       for (int rr = 0; rr < RPG; ++rr) {
         const int lr = rr * G + grp;
@@ -474,7 +594,7 @@ __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typ
         const bool nat = (native_mask >> ((sweep0 + rr) & 31)) & 1u;
         for (int32_t c = lane * VEC; c < m; c += LANES * VEC) {
           T y[VEC];
-          Arith::template row<VEC>(gci, gv, vn, j0, j1, m, c, X, y, nat);
+          Arith::template row_g<VEC>(A, ab, j0, j1, m, c, X, y, nat);
           epi(r0 + lr, c, y);
         }
       }

@@ -21,7 +21,19 @@ ens_status solve_f64_split(const ens_matrix *M, int32_t m, const double *B, doub
                            const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s);
 ens_status solve_f64_native(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
                             const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s);
+ens_status solve_f64_hybrid(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                            const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s);
 }  // namespace solver
+
+// FP64 arithmetic of the solver's products for block width m (padded to even): native, split with
+// a native share, or the column hybrid (0, 1, 2).
+static int solver_arith(const ens_matrix *A, int32_t m) {
+  if (!use_split(A)) return 0;
+  const int mp = m == 1 ? 1 : (m + 1) / 2 * 2;
+  const int share = native_share(A, mp);
+  if (share == kShareHybrid) return mp % 2 == 0 ? 2 : 0;
+  return share >= 32 ? 0 : 1;
+}
 
 namespace {
 
@@ -66,9 +78,9 @@ void ens_default_solve_opts(ens_solve_opts *o) {
   o->cheb_lo = 2.0 / 30.0;
   o->cheb_hi = 2.0;
   o->precision = ENS_PREC_F64;
-  o->inner_tol = 1e-4;
-  o->max_outer = 30;
-  o->inner_max_iter = 1000;
+  o->inner_tol = 1e-3;
+  o->max_outer = 50;
+  o->inner_max_iter = 100;
   o->check_every = 1;
   o->x0_zero = 0;
   o->use_graph = 1;
@@ -92,8 +104,10 @@ ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_
   std::vector<std::unique_ptr<solver::SysBase>> sys;
   for (int32_t i = 0; i < nsys; ++i) {
     const ens_batch_item &it = items[i];
-    sys.emplace_back(use_split(it.A) ? solver::make_system_split(it.A, it.m, it.B, it.X, it.tol, o, s)
-                                     : solver::make_system_native(it.A, it.m, it.B, it.X, it.tol, o, s));
+    const int ar = solver_arith(it.A, it.m);
+    sys.emplace_back(ar == 2   ? solver::make_system_hybrid(it.A, it.m, it.B, it.X, it.tol, o, s)
+                     : ar == 1 ? solver::make_system_split(it.A, it.m, it.B, it.X, it.tol, o, s)
+                               : solver::make_system_native(it.A, it.m, it.B, it.X, it.tol, o, s));
   }
   cudaError_t e = cudaSuccess;
   {
@@ -149,7 +163,9 @@ ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, doub
   ens_status st = validate_solve(A, m, B, X, tol, o);
   if (st != ENS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (use_split(A)) return solver::solve_f64_split(A, m, B, X, tol, o, stats, s);
+  const int ar = solver_arith(A, m);
+  if (ar == 2) return solver::solve_f64_hybrid(A, m, B, X, tol, o, stats, s);
+  if (ar == 1) return solver::solve_f64_split(A, m, B, X, tol, o, stats, s);
   return solver::solve_f64_native(A, m, B, X, tol, o, stats, s);
 }
 

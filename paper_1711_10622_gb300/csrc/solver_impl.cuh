@@ -1205,10 +1205,13 @@ SysBase *make_system_split(const ens_matrix *M, int32_t m, const double *B, doub
                            const ens_solve_opts &o, cudaStream_t s);
 SysBase *make_system_native(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
                             const ens_solve_opts &o, cudaStream_t s);
+SysBase *make_system_hybrid(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
+                            const ens_solve_opts &o, cudaStream_t s);
 
 extern template struct Bicg<ArithF32>;
 extern template struct Bicg<ArithF64Split>;
 extern template struct Bicg<ArithF64Native>;
+extern template struct Bicg<ArithF64Hybrid>;
 
 }  // namespace solver
 }  // namespace ens

@@ -96,7 +96,7 @@ M_VALUES = [1, 2, 3, 4, 5, 7, 8, 16, 32, 33, 64]
 
 @pytest.mark.parametrize("name", list(OPS))
 @pytest.mark.parametrize("m", M_VALUES)
-@pytest.mark.parametrize("mode", ["auto", "native", "f32"])
+@pytest.mark.parametrize("mode", ["auto", "native", "hybrid", "f32"])
 def test_gspmv_parity(ens, name, m, mode):
     op = _op(name)
     X = gen.rhs_normal(op.n, m, 1000 + m)
@@ -204,7 +204,7 @@ def test_full_size_channel_sampled(ens, m):
     scale = oracle.gspmv_rows(sub, rows, np.abs(X))
     with ens.Matrix.from_operator(op) as A:
         Xd = torch.from_numpy(X).cuda()
-        for mode in ("auto", "native"):
+        for mode in ("auto", "native", "hybrid", "split"):
             A.set_f64_mode(mode)
             Yd = ens.gspmv(A, Xd)
             Y = Yd[torch.from_numpy(rows).cuda()].cpu().numpy()

@@ -28,8 +28,10 @@ def ens():
     return ens
 
 
-def _solve(ens, op, B, tol, X0=None, **kw):
+def _solve(ens, op, B, tol, X0=None, f64_mode=None, **kw):
     with ens.Matrix.from_operator(op) as A:
+        if f64_mode:
+            A.set_f64_mode(f64_mode)
         Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
         Xd = None if X0 is None else torch.from_numpy(np.ascontiguousarray(X0)).cuda()
         X, st = ens.solve_block(A, Bd, Xd, tol=tol, **kw)
@@ -79,15 +81,16 @@ def test_dense_lu_8cubed(ens):
 
 @pytest.mark.parametrize("m", [1, 2, 3, 5, 8])
 @pytest.mark.parametrize("use_graph", [1, 0])
-def test_chebyshev_cubes_small(ens, m, use_graph):
+@pytest.mark.parametrize("f64_mode", [None, "hybrid", "split", "native"])
+def test_chebyshev_cubes_small(ens, m, use_graph, f64_mode):
     """Residual bar at 1e-8; the solution comparison runs at 1e-10, where the difference between
     two converged solutions (each about cond(A) * tol from the exact one) is far below 1e-6."""
     op = gen.cubes(48, 32, 24, size=4)
     B = gen.rhs_normal(op.n, m, 40 + m, zero_mean=True)
-    Xg, st = _solve(ens, op, B, 1e-8, precond="chebyshev", use_graph=use_graph)
+    Xg, st = _solve(ens, op, B, 1e-8, precond="chebyshev", use_graph=use_graph, f64_mode=f64_mode)
     assert (st["status"] == 0).all() and np.all(st["relres"] <= 1.05e-8)
     assert np.all(_true_relres(op, B, Xg) <= 1.05e-8)
-    Xg, st = _solve(ens, op, B, 1e-10, precond="chebyshev", use_graph=use_graph)
+    Xg, st = _solve(ens, op, B, 1e-10, precond="chebyshev", use_graph=use_graph, f64_mode=f64_mode)
     _check_against_oracle(op, B, Xg, st, 1e-10, precond="chebyshev")
 
 
