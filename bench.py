@@ -372,6 +372,68 @@ def run_profile(args):
     return 0
 
 
+def run_sweep(args):
+    """Arithmetic sweep of the float64 GSpMV on the channel operator: microseconds per launch for
+    native DFMA, split-float with native shares 0..24/32, the column hybrid, the autotuned choice
+    and float32 (CUDA events around 20 launches after 3 warm-up launches, inputs resident). One
+    JSON line; the basis of the arithmetic tables in the tuning notes."""
+    import torch
+
+    import gen
+    from paper_1711_10622_gb300 import build as ens_build
+
+    ens_build.build()
+    import paper_1711_10622_gb300 as ens
+
+    dims = {"full": (256, 128, 128), "half": (128, 128, 128)}[args.profile_size]
+    op = gen.channel(*dims)
+    A = ens.Matrix.from_operator(op)
+    lib = ens.api.N.lib()
+
+    def timed(X, Y, reps=20):
+        for _ in range(3):
+            ens.gspmv(A, X, Y)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(reps):
+            ens.gspmv(A, X, Y)
+        e.record()
+        torch.cuda.synchronize()
+        return round(s.elapsed_time(e) / reps * 1e3, 1)
+
+    rows = {}
+    for m in [int(v) for v in args.profile_m.split(",")]:
+        X = torch.from_numpy(gen.rhs_normal(op.n, m, 20000 + m)).to("cuda")
+        Y = torch.empty_like(X)
+        r = {}
+        A.set_f64_mode("native")
+        r["native"] = timed(X, Y)
+        A.set_f64_mode("split")
+        for share in (0, 4, 8, 12, 16, 20, 24):
+            ens.api.N.check(lib.ens_set_native_share(A.handle, share))
+            r[f"split{share}"] = timed(X, Y)
+        ens.api.N.check(lib.ens_set_native_share(A.handle, -1))
+        if m % 2 == 0:
+            A.set_f64_mode("hybrid")
+            r["hybrid"] = timed(X, Y)
+        A.set_f64_mode("auto")
+        r["tuned_cfg"] = A.autotune(m, "f64")
+        r["tuned"] = timed(X, Y)
+        X32, Y32 = X.float(), torch.empty(op.n, m, dtype=torch.float32, device="cuda")
+        r["f32"] = timed(X32, Y32)
+        best = min((v, k) for k, v in r.items() if k not in ("f32", "tuned_cfg"))
+        r["best_f64_gbs"] = round(alg_bytes(op.n, op.nnz, m) / (best[0] * 1e-6) / 1e9)
+        r["best_f64"] = best[1]
+        r["f32_gbs"] = round(alg_bytes(op.n, op.nnz, m, sv=4, sx=4) / (r["f32"] * 1e-6) / 1e9)
+        rows[m] = r
+        del X, Y, X32, Y32
+        torch.cuda.empty_cache()
+    A.close()
+    print(json.dumps({"sweep": "gspmv_f64_arithmetic", "workload": "channel%dx%dx%d" % dims, "n": op.n, "nnz": op.nnz, "us": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,9 +450,12 @@ def main():
     ap.add_argument("--profile-m", default="1,8,32")
     ap.add_argument("--profile-modes", default="split,native,f32")
     ap.add_argument("--profile-share", type=int, default=-1, help="native-DFMA share (32nds) for split mode")
+    ap.add_argument("--sweep", action="store_true", help="float64 arithmetic sweep (uses --profile-size/--profile-m)")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

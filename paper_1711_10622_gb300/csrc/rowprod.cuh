@@ -148,39 +148,54 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
 
 // ------------------------------------------------------------------ split float64
 // GB300 executes FP64 arithmetic AND every float<->double conversion on a narrow FP64 pipe
-// (a few operations per clock per SM against ~250 FP32 FMAs), so the split path touches no
-// FP64 instruction per product: the double is cut into floats with integer operations only.
+// (2 DFMA per clock per SM against 128 FP32 lanes), so the split path issues no FP64 instruction
+// per product: each double is cut into two floats with integer operations and one FP32 step.
 //
-// x = hi + lo: hi takes the sign, the exponent and mantissa bits 51..29 of x (truncation), lo the
-// next 23 bits exactly (bits 5..0 of the 52-bit mantissa are dropped: |x - hi - lo| < 2^-46 |x|).
-//   hi: the funnel shift (hw:lw) << 3 puts mantissa bits 51..29 in place and the low 8 bits of
-//       the 11-bit exponent E in bits 30..23; E - 896 (the float bias shift) equals those 8 bits
-//       with bit 7 flipped for E in [896, 1151]; the sign is copied.
-//   lo: lo = F - P with P = sign(x) 2^(e-23) (float exponent of hi minus 23) and F = P carrying
-//       mantissa bits 28..6 of x; the subtraction is exact.
-// Valid for +-0 and for biased exponents E in [kSplitELo, kSplitEHi] (|x| in [2^-40, 2^60)); the
-// function returns false outside that range (tiny, huge, Inf, NaN) and the caller recomputes the
-// row segment with native DFMA. Zero gets hi = 0 explicitly (the exponent rebias would otherwise
-// turn it into 2.0); its lo is then F - P = 0 by construction.
-constexpr uint32_t kSplitELo = 983u, kSplitEHi = 1082u;
+// x = hi + lo + r with |r| < 2^-46 |x| (E = biased exponent of x):
+//   hi: sign, exponent E - 896 and mantissa bits 51..29 of x (truncation). The funnel shift
+//       (hw:lw) << 3 puts mantissa bits 51..29 in bits 22..0 and exponent bits 7..0 in bits
+//       30..23. Bit 31 must be the sign and bit 30 the top bit of E - 896, which for E in
+//       [896, 1151] is exponent bit 10 of x, i.e. bit 30 of hw: one bit select takes bits 31..30
+//       from hw and bits 29..0 from the shifted word. x = +-0 gives hi = +-0.
+//   lo: mantissa bits 28..6 of x, worth m_lo 2^(E-1069). G = 2^-23 (1 + m_lo 2^-23) is those
+//       bits under a constant exponent, and lo = (G - 2^-23) P with P = sign(x) 2^(E-1023), the
+//       sign and exponent bits of hi. The subtraction is exact (Sterbenz) and so is the scaling
+//       by a power of two (no underflow inside the window below). x = +-0 gives lo = 0.
+// The construction holds for E in [896, 1151]. A row segment takes the split path for a column
+// when every x it reads has E in [kSplitELo, kSplitELo + 127] (|x| in [2^-40, 2^88)):
+// split_range(x) is below kSplitWindow exactly for those, so one OR per element accumulates the
+// test. Zeros, tiny, huge and non-finite values fail it and the segment is recomputed with native
+// DFMA for that column.
+constexpr uint32_t kSplitELo = 983u;
+constexpr uint32_t kSplitWindow = 128u << 21;
 constexpr int32_t kSplitMaxRow = 64;
+constexpr uint32_t kSplitG = 0x34000000u;  // 2^-23
 
-__device__ __forceinline__ bool split_f64(double x, float &hi, float &lo) {
-  const uint32_t hw = (uint32_t)__double2hiint(x);
-  const uint32_t lw = (uint32_t)__double2loint(x);
-  const bool zero = ((hw & 0x7FFFFFFFu) | lw) == 0u;
-  const uint32_t fb = __funnelshift_l(lw, hw, 3);
-  const uint32_t hb = zero ? 0u : (((fb & 0x7FFFFFFFu) ^ 0x40000000u) | (hw & 0x80000000u));
-  const uint32_t pb = (hb & 0xFF800000u) - (23u << 23);
+__device__ __forceinline__ uint32_t split_hi_bits(uint32_t hw, uint32_t lw) {
+  return (__funnelshift_l(lw, hw, 3) & 0x3FFFFFFFu) | (hw & 0xC0000000u);
+}
+__device__ __forceinline__ uint32_t split_g_bits(uint32_t lw) { return ((lw >> 6) & 0x007FFFFFu) | kSplitG; }
+
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const uint32_t hb = split_hi_bits(hw, lw);
   hi = __uint_as_float(hb);
-  lo = __fsub_rn(__uint_as_float(pb | ((lw >> 6) & 0x7FFFFFu)), __uint_as_float(pb));
-  return zero || ((hw & 0x7FF00000u) - (kSplitELo << 20)) <= ((kSplitEHi - kSplitELo) << 20);
+  lo = __fmul_rn(__fsub_rn(__uint_as_float(split_g_bits(lw)), __uint_as_float(kSplitG)),
+                 __uint_as_float(hb & 0xFF800000u));
 }
 
-// With |x| and |val| in [2^-40, 2^60) (val checked once per matrix, zeros allowed) every nonzero
-// product lies in [2^-80, 2^120): its low parts stay normal floats (or fall below 2^-126, i.e.
-// 2^-46 of the smallest product, where flushing them is harmless), and a sum of at most
-// kSplitMaxRow products stays below 2^127.
+// (E - kSplitELo) << 21 plus the high mantissa bits, modulo 2^32 (the sign drops out).
+__device__ __forceinline__ uint32_t split_range(double x) {
+  return (uint32_t)__double2hiint(x) * 2u - (kSplitELo << 21);
+}
+
+// The matrix values are checked once (2^-40 <= |a| < 2^60, or a = 0), so every nonzero product
+// has magnitude >= 2^-80 and its low part stays a normal float. Products of up to 2^148 can
+// overflow the float range: the accumulators then hold Inf or NaN, which split_ok() catches.
+__device__ __forceinline__ bool split_finite(float f) { return (__float_as_uint(f) & 0x7F800000u) != 0x7F800000u; }
+__device__ __forceinline__ bool split_ok(uint32_t range_or, float hi, float lo) {
+  return range_or < kSplitWindow && split_finite(hi) && split_finite(lo);
+}
 
 // (s, e) = TwoSum(a, b): s = fl(a + b), s + e = a + b exactly (Knuth).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -261,11 +276,11 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
                                           const double *__restrict__ vn, int32_t m, int32_t c,
                                           const double *__restrict__ X, double (&y)[VEC]) {
   float sh[VEC], sl[VEC];
-  bool ok[VEC];
+  uint32_t rng[VEC];
 #pragma unroll
   for (int q = 0; q < VEC; ++q) {
     sh[q] = sl[q] = 0.f;
-    ok[q] = true;
+    rng[q] = 0u;
   }
   for (int32_t j = j0; j < j1; ++j) {
     const int32_t k = ci[j];
@@ -275,13 +290,15 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       float xh, xl;
-      ok[q] &= split_f64(x[q], xh, xl);
+      rng[q] |= split_range(x[q]);
+      split_f64(x[q], xh, xl);
       split_fma(a.x, a.y, xh, xl, sh[q], sl[q]);
     }
   }
-  bool all_ok = true;
+  bool ok[VEC], all_ok = true;
 #pragma unroll
   for (int q = 0; q < VEC; ++q) {
+    ok[q] = split_ok(rng[q], sh[q], sl[q]);
     y[q] = split_to_double(sh[q], sl[q]);
     all_ok &= ok[q];
   }
@@ -293,39 +310,58 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
   }
 }
 
-// Two columns per lane: the same arithmetic as split_fma on packed pairs. With p = ah*xh rounded,
-// the negated error terms are accumulated (fma(-ah, xh, p) = p - ah*xh exactly), which needs no
-// packed negation.
+// Two columns per lane: the same arithmetic as split_fma on packed pairs, with the low parts of
+// both X values formed by one packed subtract and multiply. With p = ah*xh rounded, the negated
+// error terms are accumulated (fma(-ah, xh, p) = p - ah*xh exactly), which needs no packed
+// negation. The X gathers of kUnroll nonzeros are issued together before any of them is used
+// (the loop is bound by gather latency, not by arithmetic); a short last group re-reads the
+// group's first address and skips the arithmetic for the missing entries.
+__device__ __forceinline__ void split_acc2(float2 a, double x0, double x1, uint64_t g23, uint64_t &sh, uint64_t &sl,
+                                           uint32_t &rng0, uint32_t &rng1) {
+  const uint32_t hw0 = (uint32_t)__double2hiint(x0), lw0 = (uint32_t)__double2loint(x0);
+  const uint32_t hw1 = (uint32_t)__double2hiint(x1), lw1 = (uint32_t)__double2loint(x1);
+  rng0 |= split_range(x0);
+  rng1 |= split_range(x1);
+  const uint32_t hb0 = split_hi_bits(hw0, lw0), hb1 = split_hi_bits(hw1, lw1);
+  const uint64_t xh = f2_pack(__uint_as_float(hb0), __uint_as_float(hb1));
+  const uint64_t g = f2_pack(__uint_as_float(split_g_bits(lw0)), __uint_as_float(split_g_bits(lw1)));
+  const uint64_t pw = f2_pack(__uint_as_float(hb0 & 0xFF800000u), __uint_as_float(hb1 & 0xFF800000u));
+  const uint64_t xl = f2_mul(f2_sub(g, g23), pw);
+  const uint64_t ah = f2_pack(a.x, a.x), nah = f2_pack(-a.x, -a.x), nal = f2_pack(-a.y, -a.y);
+  const uint64_t ph = f2_mul(ah, xh);
+  uint64_t npl = f2_fma(nah, xh, ph);  // -(ah*xh - ph)
+  npl = f2_fma(nah, xl, npl);
+  npl = f2_fma(nal, xh, npl);          // -(low part of the product)
+  const uint64_t s = f2_add(sh, ph);
+  const uint64_t bb = f2_sub(s, sh);
+  const uint64_t e = f2_add(f2_sub(sh, f2_sub(s, bb)), f2_sub(ph, bb));
+  sh = s;
+  sl = f2_add(sl, f2_sub(e, npl));
+}
+
 template <>
 __device__ __forceinline__ void row_split<2>(int32_t j0, int32_t j1, const int32_t *ci, const float2 *vs,
                                              const double *__restrict__ vn, int32_t m, int32_t c,
                                              const double *__restrict__ X, double (&y)[2]) {
   uint64_t sh = 0ull, sl = 0ull;
-  bool ok0 = true, ok1 = true;
-#pragma unroll 2
-  for (int32_t j = j0; j < j1; ++j) {
-    const int32_t k = ci[j];
-    const float2 a = vs[j];
-    double x[2];
-    load_vec<double, 2>(X + (int64_t)k * m + c, x);
-    float xh0, xl0, xh1, xl1;
-    ok0 &= split_f64(x[0], xh0, xl0);
-    ok1 &= split_f64(x[1], xh1, xl1);
-    const uint64_t xh = f2_pack(xh0, xh1), xl = f2_pack(xl0, xl1);
-    const uint64_t ah = f2_pack(a.x, a.x), nah = f2_pack(-a.x, -a.x), nal = f2_pack(-a.y, -a.y);
-    const uint64_t ph = f2_mul(ah, xh);
-    uint64_t npl = f2_fma(nah, xh, ph);  // -(ah*xh - ph)
-    npl = f2_fma(nah, xl, npl);
-    npl = f2_fma(nal, xh, npl);          // -(low part of the product)
-    const uint64_t s = f2_add(sh, ph);
-    const uint64_t bb = f2_sub(s, sh);
-    const uint64_t e = f2_add(f2_sub(sh, f2_sub(s, bb)), f2_sub(ph, bb));
-    sh = s;
-    sl = f2_add(sl, f2_sub(e, npl));
+  uint32_t rng0 = 0u, rng1 = 0u;
+  const uint64_t g23 = f2_pack(__uint_as_float(kSplitG), __uint_as_float(kSplitG));
+  for (int32_t j = j0; j < j1; j += kUnroll) {
+    const int32_t len = j1 - j;
+    double x[kUnroll][2];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int32_t k = ci[u < len ? j + u : j];
+      load_vec<double, 2>(X + (int64_t)k * m + c, x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (u < len) split_acc2(vs[j + u], x[u][0], x[u][1], g23, sh, sl, rng0, rng1);
   }
   float h0, h1, l0, l1;
   f2_unpack(sh, h0, h1);
   f2_unpack(sl, l0, l1);
+  const bool ok0 = split_ok(rng0, h0, l0), ok1 = split_ok(rng1, h1, l1);
   y[0] = split_to_double(h0, l0);
   y[1] = split_to_double(h1, l1);
   if (!(ok0 && ok1)) {
@@ -372,40 +408,30 @@ __device__ __forceinline__ void row_hybrid<2>(int32_t j0, int32_t j1, const int3
                                               double (&y)[2]) {
   double acc = 0.0;
   float sh = 0.f, sl = 0.f;
-  bool ok = true;
-  int32_t j = j0;
-  for (; j + kUnroll <= j1; j += kUnroll) {
-    int32_t k[kUnroll];
-    double ad[kUnroll];
-    float2 as[kUnroll];
+  uint32_t rng = 0u;
+  for (int32_t j = j0; j < j1; j += kUnroll) {
+    const int32_t len = j1 - j;
     double x[kUnroll][2];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      k[u] = ci[j + u];
-      ad[u] = vd[j + u];
-      as[u] = vs[j + u];
+      const int32_t k = ci[u < len ? j + u : j];
+      load_vec<double, 2>(X + (int64_t)k * m + c, x[u]);
     }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) load_vec<double, 2>(X + (int64_t)k[u] * m + c, x[u]);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      acc = fma(ad[u], x[u][0], acc);
-      float xh, xl;
-      ok &= split_f64(x[u][1], xh, xl);
-      split_fma(as[u].x, as[u].y, xh, xl, sh, sl);
+      if (u < len) {
+        acc = fma(vd[j + u], x[u][0], acc);
+        float xh, xl;
+        rng |= split_range(x[u][1]);
+        split_f64(x[u][1], xh, xl);
+        const float2 a = vs[j + u];
+        split_fma(a.x, a.y, xh, xl, sh, sl);
+      }
     }
-  }
-  for (; j < j1; ++j) {
-    double x[2];
-    load_vec<double, 2>(X + (int64_t)ci[j] * m + c, x);
-    acc = fma(vd[j], x[0], acc);
-    float xh, xl;
-    ok &= split_f64(x[1], xh, xl);
-    split_fma(vs[j].x, vs[j].y, xh, xl, sh, sl);
   }
   y[0] = acc;
   y[1] = split_to_double(sh, sl);
-  if (!ok) {
+  if (!split_ok(rng, sh, sl)) {
     double z = 0.0;
     for (int32_t jj = j0; jj < j1; ++jj) z = fma(vd[jj], __ldg(X + (int64_t)ci[jj] * m + c + 1), z);
     y[1] = z;

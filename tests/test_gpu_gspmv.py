@@ -150,6 +150,16 @@ def test_split_range_fallbacks(ens):
     with ens.Matrix.from_operator(op) as A:
         Y = ens.gspmv(A, torch.from_numpy(X).cuda()).cpu().numpy()
         _check_f64(op, X, Y)
+    # products above the float range (|a| ~ 1e13, |x| ~ 3e25): the split accumulators overflow
+    # and those row segments are recomputed natively
+    big = gen.Operator(op.name, op.shape, op.bcs, op.row_ptr, op.col_idx, op.val * 1e15, op.singular)
+    Xb = X.copy()
+    Xb[::61, 6] = 3e25
+    Xb[::67, 2] = 1e30  # above the split window
+    with ens.Matrix.from_operator(big) as A:
+        Y = ens.gspmv(A, torch.from_numpy(Xb).cuda()).cpu().numpy()
+        assert np.all(np.isfinite(Y))
+        _check_f64(big, Xb, Y)
     # matrix values outside the split range: the whole product is native
     scaled = gen.Operator(op.name, op.shape, op.bcs, op.row_ptr, op.col_idx, op.val * 1e-18, op.singular)
     with ens.Matrix.from_operator(scaled) as A:
@@ -235,7 +245,7 @@ def test_autotune_then_parity(ens):
             for dt in ("f64", "f32"):
                 r = A.autotune(m, dt)
                 assert r["lanes"] >= 1 and r["best_us"] > 0
-                assert r["share"] in (0, 8, 16, 24, 32) or dt == "f32"
+                assert r["share"] in (0, 8, 16, 24, 32, 64) or dt == "f32"  # 64: column hybrid
                 X = gen.rhs_normal(op.n, m, 500 + m)
                 if dt == "f64":
                     Y = ens.gspmv(A, torch.from_numpy(X).cuda()).cpu().numpy()
