@@ -19,6 +19,7 @@ from .workloads import (
     serving_requests,
     poisson_arrivals,
 )
+from .fields import Grid, grid_of, predictor_velocity
 
 __all__ = [
     "Operator",
@@ -34,4 +35,7 @@ __all__ = [
     "serving_operators",
     "serving_requests",
     "poisson_arrivals",
+    "Grid",
+    "grid_of",
+    "predictor_velocity",
 ]

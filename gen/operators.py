@@ -213,4 +213,6 @@ def fv_poisson(
         cell_of_row=None if solid is None else np.nonzero(fluid_flat)[0].astype(np.int64),
     )
     op.meta["dy_ratio"] = float(wy.max() / wy.min())
+    op.meta["nodes"] = tuple(np.array(a, dtype=np.float64) for a in nodes)
+    op.meta["solid"] = None if solid is None else ~fluid
     return op

@@ -53,6 +53,9 @@ def lib():
         L.oracle_solve_block.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _vp]
         L.oracle_lu_solve.argtypes = [ctypes.c_int, _vp, _vp]
         L.oracle_lu_solve.restype = ctypes.c_int
+        grid_args = [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double]
+        L.oracle_divergence.argtypes = grid_args + [_vp, _vp, _vp, _vp]
+        L.oracle_grad_correct.argtypes = grid_args + [_vp, _vp, _vp, _vp]
         _lib = L
     return _lib
 
@@ -155,6 +158,37 @@ def lu_solve(Adense: np.ndarray, b: np.ndarray) -> np.ndarray:
     if lib().oracle_lu_solve(a.shape[0], _p(a), _p(x)) != 0:
         raise np.linalg.LinAlgError("zero pivot")
     return x
+
+
+def _grid_args(grid):
+    nx, ny, nz = grid.shape
+    xn, yn, zn = (np.ascontiguousarray(a, dtype=np.float64) for a in grid.nodes)
+    bc = np.ascontiguousarray(grid.bc_codes, dtype=np.int32)
+    rows = np.ascontiguousarray(grid.row_of_cell, dtype=np.int64)
+    keep = (xn, yn, zn, bc, rows)
+    return keep, [nx, ny, nz, _p(xn), _p(yn), _p(zn), _p(bc), _p(rows)]
+
+
+def divergence(grid, U, V, W, scale: float = 1.0) -> np.ndarray:
+    """scale * (D u) per fluid-cell row, (n, m): the outward face-flux sum of the staggered field
+    (U, V, W) (projection.c; Section 2.2, Eq. eq3's right-hand side with scale = 1/tau up to the
+    sign convention A = -L)."""
+    comps = [np.ascontiguousarray(c, dtype=np.float64) for c in (U, V, W)]
+    m = comps[0].shape[1]
+    out = np.zeros((grid.n, m))
+    keep, args = _grid_args(grid)
+    lib().oracle_divergence(*args, m, float(scale), *(_p(c) for c in comps), _p(out))
+    return out
+
+
+def grad_correct(grid, P, U, V, W, tau: float):
+    """(U, V, W) - tau * G p on the open faces (Section 2.2, Eq. eq2); returns new arrays."""
+    comps = [np.array(c, dtype=np.float64, order="C", copy=True) for c in (U, V, W)]
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    m = P.shape[1]
+    keep, args = _grid_args(grid)
+    lib().oracle_grad_correct(*args, m, float(tau), _p(P), *(_p(c) for c in comps))
+    return tuple(comps)
 
 
 def relerr_rows(Y: np.ndarray, Yref: np.ndarray, A, X: np.ndarray) -> float:
