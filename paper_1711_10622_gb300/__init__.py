@@ -2,10 +2,24 @@
 
 m pressure-Poisson solves that share one sparse matrix: the generalised SpMV Y = A X on an
 n x m row-interleaved block, inside a multi-RHS BiCGStab with block vector updates, per-column
-dot products and a Chebyshev polynomial preconditioner. The computation lives in the C-ABI
+dot products and a Chebyshev polynomial preconditioner, plus the projection step around the
+solve (divergence right-hand sides, pressure-gradient correction). The computation lives in the C-ABI
 library libensemble_solve.so (include/ensemble_solve.h); this package is its Python binding.
 """
 
-from .api import COL_STATUS, EnsError, Matrix, gspmv, gspmv_host, solve_batch, solve_block, solve_opts, version  # noqa: F401
+from .api import COL_STATUS, EnsError, Grid, Matrix, divergence, grad_correct, gspmv, gspmv_host, solve_batch, solve_block, solve_opts, version  # noqa: F401
 
-__all__ = ["Matrix", "EnsError", "gspmv", "gspmv_host", "solve_block", "solve_batch", "solve_opts", "COL_STATUS", "version"]
+__all__ = [
+    "Matrix",
+    "Grid",
+    "EnsError",
+    "gspmv",
+    "gspmv_host",
+    "solve_block",
+    "solve_batch",
+    "solve_opts",
+    "divergence",
+    "grad_correct",
+    "COL_STATUS",
+    "version",
+]

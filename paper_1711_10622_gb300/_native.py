@@ -124,6 +124,11 @@ def lib():
             [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp],
         ),
         "ens_solve_batch": (_i32, [_i32, ctypes.POINTER(BatchItem), ctypes.POINTER(SolveOpts), _vp]),
+        "ens_create_grid": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+        "ens_destroy_grid": (_i32, [_vp]),
+        "ens_grid_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+        "ens_divergence": (_i32, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]),
+        "ens_grad_correct": (_i32, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]),
         "ens_last_error": (ctypes.c_char_p, []),
         "ens_version": (ctypes.c_char_p, []),
     }

@@ -278,3 +278,95 @@ def solve_batch(systems, stream=None, **opts):
 
 def version() -> str:
     return N.lib().ens_version().decode()
+
+
+class Grid:
+    """A device copy of a staggered grid for the projection step (ens_create_grid): node
+    coordinates, boundary types per direction and an optional solid-cell mask."""
+
+    BC = {"neumann": 0, "wall": 0, "periodic": 1, "dirichlet": 2}
+
+    def __init__(self, shape, nodes, bcs, solid=None, stream=None):
+        nx, ny, nz = (int(v) for v in shape)
+        xn, yn, zn = (np.ascontiguousarray(a, dtype=np.float64) for a in nodes)
+        bc = np.array([self.BC[b] if isinstance(b, str) else int(b) for b in bcs], dtype=np.int32)
+        sp = None if solid is None else np.ascontiguousarray(np.asarray(solid, dtype=bool).reshape(-1), dtype=np.uint8)
+        for a, want in ((xn, nx + 1), (yn, ny + 1), (zn, nz + 1)):
+            if a.shape != (want,):
+                raise ValueError("node arrays must have N + 1 entries per direction")
+        if sp is not None and sp.shape != (nx * ny * nz,):
+            raise ValueError("solid mask must have nx * ny * nz entries")
+        h = ctypes.c_void_p()
+        vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        N.check(
+            N.lib().ens_create_grid(nx, ny, nz, vp(xn), vp(yn), vp(zn), vp(bc), vp(sp), _stream_handle(stream), ctypes.byref(h))
+        )
+        self._h = h
+        rows, faces = ctypes.c_int64(), (ctypes.c_int64 * 3)()
+        N.check(N.lib().ens_grid_info(self._h, ctypes.byref(rows), faces))
+        self.n = rows.value
+        self.nfaces = tuple(int(f) for f in faces)
+
+    @classmethod
+    def from_grid(cls, g, stream=None):
+        """From a gen.Grid (the grid a gen operator was assembled on)."""
+        return cls(g.shape, g.nodes, g.bcs, g.solid, stream=stream)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("grid has been destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            N.check(N.lib().ens_destroy_grid(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _check_faces(G: Grid, comps, m=None):
+    for d, t in enumerate(comps):
+        if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_floating_point() or not t.is_contiguous() or t.dim() != 2:
+            raise ValueError("velocity components must be contiguous (faces, m) float64 CUDA tensors")
+        if t.shape[0] != G.nfaces[d] or (m is not None and t.shape[1] != m):
+            raise ValueError(f"component {d} must have shape ({G.nfaces[d]}, m)")
+
+
+def divergence(G: Grid, U, V, W, scale: float = 1.0, D=None, stream=None):
+    """D = scale * div(u) per fluid-cell row (ens_divergence); U, V, W are (faces_d, m) tensors."""
+    import torch
+
+    m = U.shape[1]
+    _check_faces(G, (U, V, W), m)
+    if D is None:
+        D = torch.empty(G.n, m, dtype=torch.float64, device=U.device)
+    if D.shape != (G.n, m) or D.dtype != torch.float64 or not D.is_contiguous():
+        raise ValueError("D must be a contiguous (n, m) float64 tensor")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    N.check(N.lib().ens_divergence(G.handle, m, float(scale), ptr(U), ptr(V), ptr(W), ptr(D), _stream_handle(stream)))
+    return D
+
+
+def grad_correct(G: Grid, P, U, V, W, tau: float, stream=None):
+    """U, V, W -= tau * grad(P) on the open faces, in place (ens_grad_correct)."""
+    import torch
+
+    m = P.shape[1]
+    _check_faces(G, (U, V, W), m)
+    if P.shape != (G.n, m) or P.dtype != torch.float64 or not P.is_contiguous() or not P.is_cuda:
+        raise ValueError("P must be a contiguous (n, m) float64 CUDA tensor")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    N.check(N.lib().ens_grad_correct(G.handle, m, float(tau), ptr(P), ptr(U), ptr(V), ptr(W), _stream_handle(stream)))
+    return U, V, W

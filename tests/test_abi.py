@@ -100,3 +100,44 @@ def test_null_arguments_rejected(native):
     assert L.ens_destroy_matrix(None) == native.ENS_OK
     assert L.ens_set_f64_mode(None, 0) == native.ENS_ERR_INVALID
     assert L.ens_matrix_info(None, None, None, None) == native.ENS_ERR_INVALID
+
+
+def _create_grid(native, nx, ny, nz, nodes=None, bc=(1, 0, 1), solid=None, out=True):
+    L = native.lib()
+    if nodes is None:
+        nodes = [np.linspace(0.0, 1.0, k + 1) for k in (nx, ny, nz)]
+    nodes = [np.ascontiguousarray(a, dtype=np.float64) for a in nodes]
+    bca = np.ascontiguousarray(bc, dtype=np.int32)
+    sp = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    st = L.ens_create_grid(
+        nx, ny, nz, *(a.ctypes.data_as(ctypes.c_void_p) for a in nodes), bca.ctypes.data_as(ctypes.c_void_p),
+        None if sp is None else sp.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(h) if out else None,
+    )
+    return st, L.ens_last_error().decode()
+
+
+@pytest.mark.parametrize(
+    "args,msg",
+    [
+        (dict(nx=0, ny=4, nz=4), "dimensions"),
+        (dict(nx=2, ny=4, nz=4), "periodic direction 0"),
+        (dict(nx=4, ny=4, nz=4, bc=(1, 7, 1)), "unknown boundary code"),
+        (dict(nx=4, ny=4, nz=4, nodes=[np.linspace(1, 0, 5), np.linspace(0, 1, 5), np.linspace(0, 1, 5)]), "increasing"),
+        (dict(nx=4, ny=4, nz=4, nodes=[np.array([0, 1, np.nan, 3, 4.0]), np.linspace(0, 1, 5), np.linspace(0, 1, 5)]), "finite"),
+        (dict(nx=4, ny=4, nz=4, solid=np.ones(64)), "solid"),
+        (dict(nx=4, ny=4, nz=4, out=False), "out is NULL"),
+    ],
+)
+def test_create_grid_rejects_bad_descriptions(native, args, msg):
+    st, err = _create_grid(native, **args)
+    assert st == native.ENS_ERR_INVALID
+    assert msg in err
+
+
+def test_projection_null_arguments_rejected(native):
+    L = native.lib()
+    assert L.ens_divergence(None, 2, 1.0, None, None, None, None, None) == native.ENS_ERR_INVALID
+    assert L.ens_grad_correct(None, 2, 1.0, None, None, None, None, None) == native.ENS_ERR_INVALID
+    assert L.ens_grid_info(None, None, None) == native.ENS_ERR_INVALID
+    assert L.ens_destroy_grid(None) == native.ENS_OK
