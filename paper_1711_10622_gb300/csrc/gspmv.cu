@@ -30,9 +30,12 @@ MatView view_of(const ens_matrix *A) {
   return MatView{(int32_t)A->n, A->row, A->col, A->val, A->val32, A->valsplit, A->dinv, A->dinv32};
 }
 
+#ifndef ENS_GSPMV_MIN_BLOCKS
+#define ENS_GSPMV_MIN_BLOCKS 1
+#endif
 // Tiled GSpMV: CSR segments staged in shared memory (tile_rows), Y written with streaming stores.
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, ENS_GSPMV_MIN_BLOCKS)
     gspmv_kernel(MatView A, int32_t m, const typename Arith::T *__restrict__ X, typename Arith::T *__restrict__ Y,
                  uint32_t native_mask) {
   using T = typename Arith::T;

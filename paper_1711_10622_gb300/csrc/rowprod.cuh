@@ -282,17 +282,26 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
     sh[q] = sl[q] = 0.f;
     rng[q] = 0u;
   }
-  for (int32_t j = j0; j < j1; ++j) {
-    const int32_t k = ci[j];
-    const float2 a = vs[j];
-    double x[VEC];
-    load_vec<double, VEC>(X + (int64_t)k * m + c, x);
+  for (int32_t j = j0; j < j1; j += kUnroll) {
+    const int32_t len = j1 - j;
+    double x[kUnroll][VEC];
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) {
-      float xh, xl;
-      rng[q] |= split_range(x[q]);
-      split_f64(x[q], xh, xl);
-      split_fma(a.x, a.y, xh, xl, sh[q], sl[q]);
+    for (int u = 0; u < kUnroll; ++u) {
+      const int32_t k = ci[u < len ? j + u : j];
+      load_vec<double, VEC>(X + (int64_t)k * m + c, x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (u < len) {
+        const float2 a = vs[j + u];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          float xh, xl;
+          rng[q] |= split_range(x[u][q]);
+          split_f64(x[u][q], xh, xl);
+          split_fma(a.x, a.y, xh, xl, sh[q], sl[q]);
+        }
+      }
     }
   }
   bool ok[VEC], all_ok = true;
@@ -310,14 +319,23 @@ __device__ __forceinline__ void row_split(int32_t j0, int32_t j1, const int32_t 
   }
 }
 
-// Two columns per lane: the same arithmetic as split_fma on packed pairs, with the low parts of
-// both X values formed by one packed subtract and multiply. With p = ah*xh rounded, the negated
-// error terms are accumulated (fma(-ah, xh, p) = p - ah*xh exactly), which needs no packed
-// negation. The X gathers of kUnroll nonzeros are issued together before any of them is used
-// (the loop is bound by gather latency, not by arithmetic); a short last group re-reads the
-// group's first address and skips the arithmetic for the missing entries.
-__device__ __forceinline__ void split_acc2(float2 a, double x0, double x1, uint64_t g23, uint64_t &sh, uint64_t &sl,
-                                           uint32_t &rng0, uint32_t &rng1) {
+// Two columns per lane, packed f32x2 arithmetic. A nonzero's matrix value enters as the pairs
+// AH = (ah, ah) and AL = (al, al) (the split tile stores them that way, so one 16-byte shared load
+// yields both), the X values as XH = (xh0, xh1) and XL = (xl0, xl1). Per nonzero:
+//   PH = AH * XH (rounded), PL = AH*XH - PH (exact, one FMA against -PH) + AH*XL + AL*XH,
+//   (SH, E) = TwoSum(SH, PH), SL += E + PL.
+// Full groups of kUnroll nonzeros run without any predicate; the last 1..kUnroll-1 nonzeros run
+// as one group whose missing entries re-read the group's first X row and carry a zero matrix
+// value (an exact no-op: 0 * x adds +-0 to both accumulators; a non-finite x there is also in
+// slot 0 and already fails the range test).
+struct SplitPair {
+  uint64_t ah, al;
+};
+__device__ __forceinline__ SplitPair split_pair(const float4 &v) { return {f2_pack(v.x, v.y), f2_pack(v.z, v.w)}; }
+__device__ __forceinline__ SplitPair split_pair(const float2 &v) { return {f2_pack(v.x, v.x), f2_pack(v.y, v.y)}; }
+
+__device__ __forceinline__ void split_acc2(const SplitPair &a, double x0, double x1, uint64_t g23, uint64_t &sh,
+                                           uint64_t &sl, uint32_t &rng0, uint32_t &rng1) {
   const uint32_t hw0 = (uint32_t)__double2hiint(x0), lw0 = (uint32_t)__double2loint(x0);
   const uint32_t hw1 = (uint32_t)__double2hiint(x1), lw1 = (uint32_t)__double2loint(x1);
   rng0 |= split_range(x0);
@@ -327,36 +345,56 @@ __device__ __forceinline__ void split_acc2(float2 a, double x0, double x1, uint6
   const uint64_t g = f2_pack(__uint_as_float(split_g_bits(lw0)), __uint_as_float(split_g_bits(lw1)));
   const uint64_t pw = f2_pack(__uint_as_float(hb0 & 0xFF800000u), __uint_as_float(hb1 & 0xFF800000u));
   const uint64_t xl = f2_mul(f2_sub(g, g23), pw);
-  const uint64_t ah = f2_pack(a.x, a.x), nah = f2_pack(-a.x, -a.x), nal = f2_pack(-a.y, -a.y);
-  const uint64_t ph = f2_mul(ah, xh);
-  uint64_t npl = f2_fma(nah, xh, ph);  // -(ah*xh - ph)
-  npl = f2_fma(nah, xl, npl);
-  npl = f2_fma(nal, xh, npl);          // -(low part of the product)
+  const uint64_t ph = f2_mul(a.ah, xh);
+  // exact rounding error of ah*xh: fma(ah, xh, -ph), with -ph formed by flipping both sign bits.
+  // (Forming -ph as the packed difference 0 - ph lost this error term on sm_103a in a GPU check
+  // against the scalar form; the bit flip is exact and the result matches the scalar form.)
+  uint64_t pl = f2_fma(a.ah, xh, ph ^ 0x8000000080000000ull);
+  pl = f2_fma(a.ah, xl, pl);
+  pl = f2_fma(a.al, xh, pl);
   const uint64_t s = f2_add(sh, ph);
   const uint64_t bb = f2_sub(s, sh);
   const uint64_t e = f2_add(f2_sub(sh, f2_sub(s, bb)), f2_sub(ph, bb));
   sh = s;
-  sl = f2_add(sl, f2_sub(e, npl));
+  sl = f2_add(sl, f2_add(e, pl));
 }
 
-template <>
-__device__ __forceinline__ void row_split<2>(int32_t j0, int32_t j1, const int32_t *ci, const float2 *vs,
-                                             const double *__restrict__ vn, int32_t m, int32_t c,
-                                             const double *__restrict__ X, double (&y)[2]) {
+// X row k at the lane's column offset: one wide multiply-add on byte offsets.
+__device__ __forceinline__ const double2 *xrow(const char *xc, int32_t k, uint32_t row_bytes) {
+  return reinterpret_cast<const double2 *>(xc + (uint64_t)(uint32_t)k * row_bytes);
+}
+
+template <typename AV>
+__device__ __forceinline__ void row_split2(int32_t j0, int32_t j1, const int32_t *ci, const AV *va,
+                                           const double *__restrict__ vn, int32_t m, int32_t c,
+                                           const double *__restrict__ X, double (&y)[2]) {
   uint64_t sh = 0ull, sl = 0ull;
   uint32_t rng0 = 0u, rng1 = 0u;
   const uint64_t g23 = f2_pack(__uint_as_float(kSplitG), __uint_as_float(kSplitG));
-  for (int32_t j = j0; j < j1; j += kUnroll) {
-    const int32_t len = j1 - j;
-    double x[kUnroll][2];
+  const char *xc = reinterpret_cast<const char *>(X + c);
+  const uint32_t rb = (uint32_t)m * 8u;
+  int32_t j = j0;
+  for (; j + kUnroll <= j1; j += kUnroll) {
+    double2 x[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int32_t k = ci[u < len ? j + u : j];
-      load_vec<double, 2>(X + (int64_t)k * m + c, x[u]);
+    for (int u = 0; u < kUnroll; ++u) x[u] = __ldg(xrow(xc, ci[j + u], rb));
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) split_acc2(split_pair(va[j + u]), x[u].x, x[u].y, g23, sh, sl, rng0, rng1);
+  }
+  if (j < j1) {
+    const int32_t len = j1 - j;
+    double2 x[kUnroll - 1];
+    SplitPair a[kUnroll - 1];
+#pragma unroll
+    for (int u = 0; u < kUnroll - 1; ++u) {
+      const bool v = u < len;
+      const int32_t jj = v ? j + u : j;
+      x[u] = __ldg(xrow(xc, ci[jj], rb));
+      a[u] = split_pair(va[jj]);
+      if (!v) a[u] = SplitPair{0ull, 0ull};
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (u < len) split_acc2(vs[j + u], x[u][0], x[u][1], g23, sh, sl, rng0, rng1);
+    for (int u = 0; u < kUnroll - 1; ++u) split_acc2(a[u], x[u].x, x[u].y, g23, sh, sl, rng0, rng1);
   }
   float h0, h1, l0, l1;
   f2_unpack(sh, h0, h1);
@@ -487,28 +525,46 @@ struct ArithF64Native {
   }
   __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
 };
+// Split tile: each value as (ah, ah, al, al), the operand pairs of the packed arithmetic.
+struct SplitTile {
+  int32_t rp[kTileRows + 4];
+  int32_t ci[kTileNnz];
+  float4 va[kTileNnz];
+};
 struct ArithF64Split {
   using T = double;
-  using Tile = TileSmem<float2>;
+  using Tile = SplitTile;
   __device__ __forceinline__ static void stage(Tile &sm, const MatView &A, int32_t ab, int32_t ae) {
     stage16<int32_t>(sm.ci, A.ci + ab, ae - ab);
-    stage16<float2>(sm.va, A.vs + ab, ae - ab);
+    const int32_t n16 = (ae - ab) / 2;  // two (hi, lo) pairs per 16 bytes
+    const float4 *src = reinterpret_cast<const float4 *>(A.vs + ab);
+    for (int32_t t = threadIdx.x; t < n16; t += blockDim.x) {
+      const float4 q = __ldcs(src + t);
+      sm.va[2 * t] = make_float4(q.x, q.x, q.y, q.y);
+      sm.va[2 * t + 1] = make_float4(q.z, q.z, q.w, q.w);
+    }
   }
   template <int VEC>
   __device__ __forceinline__ static void row_s(const Tile &sm, const MatView &A, int32_t ab, int32_t j0, int32_t j1,
                                                int32_t m, int32_t c, const double *X, double (&y)[VEC], bool native) {
-    if (native)
+    if (native) {
       row_native_f64<VEC>(j0, j1, sm.ci, A.val + ab, m, c, X, y);
-    else
-      row_split<VEC>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
+    } else if constexpr (VEC == 2) {
+      row_split2<float4>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
+    } else {
+      row_split<VEC>(j0, j1, sm.ci, A.vs + ab, A.val + ab, m, c, X, y);
+    }
   }
   template <int VEC>
   __device__ __forceinline__ static void row_g(const MatView &A, int32_t ab, int32_t j0, int32_t j1, int32_t m,
                                                int32_t c, const double *X, double (&y)[VEC], bool native) {
-    if (native)
+    if (native) {
       row_native_f64<VEC>(j0, j1, A.ci + ab, A.val + ab, m, c, X, y);
-    else
+    } else if constexpr (VEC == 2) {
+      row_split2<float2>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
+    } else {
       row_split<VEC>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
+    }
   }
   __device__ __forceinline__ static double dinv(const MatView &A, int64_t i) { return __ldg(A.dinv + i); }
 };
