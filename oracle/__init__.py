@@ -37,6 +37,7 @@ class _Opts(ctypes.Structure):
         ("cheb_lo", ctypes.c_double),
         ("cheb_hi", ctypes.c_double),
         ("singular", ctypes.c_int),
+        ("amg", ctypes.c_void_p),
     ]
 
 
@@ -53,6 +54,13 @@ def lib():
         L.oracle_solve_block.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _vp]
         L.oracle_lu_solve.argtypes = [ctypes.c_int, _vp, _vp]
         L.oracle_lu_solve.restype = ctypes.c_int
+        L.oracle_amg_setup.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        L.oracle_amg_setup.restype = _vp
+        L.oracle_amg_free.argtypes = [_vp]
+        L.oracle_amg_levels.argtypes = [_vp, _vp, _vp]
+        L.oracle_amg_levels.restype = ctypes.c_int
+        L.oracle_amg_level.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.oracle_amg_vcycle.argtypes = [_vp, _vp, _vp]
         grid_args = [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double]
         L.oracle_divergence.argtypes = grid_args + [_vp, _vp, _vp, _vp]
         L.oracle_grad_correct.argtypes = grid_args + [_vp, _vp, _vp, _vp]
@@ -106,15 +114,70 @@ def chebyshev(A, r: np.ndarray, lo=DEFAULT_CHEB_LO, hi=DEFAULT_CHEB_HI, steps=DE
     return z
 
 
-def _opts(max_iter, precond, singular, cheb_lo, cheb_hi, cheb_steps):
+def _opts(max_iter, precond, singular, cheb_lo, cheb_hi, cheb_steps, amg=None):
+    code = {"none": 0, "chebyshev": 1, "amg": 2}[precond]
+    if code == 2 and amg is None:
+        raise ValueError("precond='amg' needs the hierarchy (amg=oracle.AMG(...))")
     return _Opts(
         max_iter=max_iter,
-        precond={"none": 0, "chebyshev": 1}[precond],
+        precond=code,
         cheb_steps=cheb_steps,
         cheb_lo=cheb_lo,
         cheb_hi=cheb_hi,
         singular=int(bool(singular)),
+        amg=None if amg is None else amg.handle,
     )
+
+
+AMG_DEFAULTS = dict(theta=0.08, max_levels=8, coarse_size=512, smooth=2, coarse=16)
+
+
+class AMG:
+    """Aggregation multigrid hierarchy of the oracle (amg.c): plain aggregation, Galerkin coarse
+    operators P^T A P, Chebyshev smoothing; vcycle() applies one V-cycle per column."""
+
+    def __init__(self, A, theta=0.08, max_levels=8, coarse_size=512, lo=DEFAULT_CHEB_LO, hi=DEFAULT_CHEB_HI, smooth=2, coarse=16):
+        row, col, val = _csr(A)
+        self._keep = (row, col, val)
+        self.handle = lib().oracle_amg_setup(row.shape[0] - 1, _p(row), _p(col), _p(val), float(theta), int(max_levels),
+                                             int(coarse_size), float(lo), float(hi), int(smooth), int(coarse))
+        n = np.zeros(16, dtype=np.int64)
+        nnz = np.zeros(16, dtype=np.int64)
+        self.nlev = lib().oracle_amg_levels(self.handle, _p(n), _p(nnz))
+        self.sizes = [(int(n[l]), int(nnz[l])) for l in range(self.nlev)]
+
+    def level(self, l):
+        """(row_ptr, col_idx, val, agg) of level l; agg is None on the coarsest level."""
+        nl, nz = self.sizes[l]
+        row = np.zeros(nl + 1, dtype=np.int32)
+        col = np.zeros(max(nz, 1), dtype=np.int32)
+        val = np.zeros(max(nz, 1))
+        agg = np.full(nl, -1, dtype=np.int32) if l < self.nlev - 1 else None
+        lib().oracle_amg_level(self.handle, l, _p(row), _p(col), _p(val), None if agg is None else _p(agg))
+        return row, col[:nz], val[:nz], agg
+
+    def vcycle(self, R: np.ndarray) -> np.ndarray:
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        one = R.ndim == 1
+        R2 = R[:, None] if one else R
+        Z = np.zeros_like(R2)
+        for l in range(R2.shape[1]):
+            r = np.ascontiguousarray(R2[:, l])
+            z = np.zeros_like(r)
+            lib().oracle_amg_vcycle(self.handle, _p(r), _p(z))
+            Z[:, l] = z
+        return Z[:, 0] if one else Z
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().oracle_amg_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_block(
@@ -128,8 +191,10 @@ def solve_block(
     cheb_lo=DEFAULT_CHEB_LO,
     cheb_hi=DEFAULT_CHEB_HI,
     cheb_steps=DEFAULT_CHEB_STEPS,
+    amg=None,
 ):
-    """m independent BiCGStab solves A x_l = b_l (Section 2.2 / 4.1).
+    """m independent BiCGStab solves A x_l = b_l (Section 2.2 / 4.1); precond 'none', 'chebyshev'
+    or 'amg' (with amg = an oracle.AMG hierarchy of A).
 
     Returns (X, iters[m], relres[m], status[m]); relres is the true residual at exit.
     """
@@ -144,7 +209,7 @@ def solve_block(
     relres = np.zeros(m, dtype=np.float64)
     status = np.zeros(m, dtype=np.int32)
     sing = A.singular if singular is None else singular
-    o = _opts(max_iter, precond, sing, cheb_lo, cheb_hi, cheb_steps)
+    o = _opts(max_iter, precond, sing, cheb_lo, cheb_hi, cheb_steps, amg)
     lib().oracle_solve_block(
         n, _p(row), _p(col), _p(val), m, _p(B), _p(X), _p(tolv), ctypes.byref(o), _p(iters), _p(relres), _p(status)
     )

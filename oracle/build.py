@@ -11,7 +11,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRCS = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "projection.c")]
+SRCS = [os.path.join(HERE, f) for f in ("oracle.c", "projection.c", "amg.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 

@@ -21,6 +21,7 @@
  *   oracle_solve_block m independent BiCGStab solves, one per column (Section 2.2: m pressure
  *                      solves share the matrix; only the right-hand sides differ).
  *   oracle_lu_solve    dense LU with partial pivoting (textbook), used to pin the solver.
+ * The aggregation multigrid preconditioner (precond 2) lives in amg.c.
  */
 #include <math.h>
 #include <stdint.h>
@@ -108,16 +109,21 @@ void oracle_chebyshev(int64_t n, const int32_t *row, const int32_t *col, const d
 
 typedef struct {
   int max_iter;
-  int precond;   /* 0 none, 1 Chebyshev */
+  int precond;   /* 0 none, 1 Chebyshev, 2 aggregation V-cycle (amg.c) */
   int cheb_steps;
   double cheb_lo, cheb_hi;
   int singular;  /* 1: constants span the null space; check compatibility, zero-mean x at exit */
+  const void *amg; /* precond 2: the hierarchy from oracle_amg_setup for this matrix */
 } oracle_opts;
+
+void oracle_amg_vcycle(const void *h, const double *r, double *z);
 
 static void apply_prec(const oracle_opts *o, int64_t n, const int32_t *row, const int32_t *col,
                        const double *val, const double *in, double *out) {
   if (o->precond == 1)
     oracle_chebyshev(n, row, col, val, in, out, o->cheb_lo, o->cheb_hi, o->cheb_steps);
+  else if (o->precond == 2)
+    oracle_amg_vcycle(o->amg, in, out);
   else
     memcpy(out, in, sizeof(double) * n);
 }
