@@ -17,6 +17,8 @@
 //     whose X values fall outside the split range are recomputed with native DFMA.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cstdint>
 #include <vector>
 
@@ -30,17 +32,34 @@ MatView view_of(const ens_matrix *A) {
   return MatView{(int32_t)A->n, A->row, A->col, A->val, A->val32, A->valsplit, A->dinv, A->dinv32};
 }
 
-#ifndef ENS_GSPMV_MIN_BLOCKS
-#define ENS_GSPMV_MIN_BLOCKS 1
-#endif
 // Tiled GSpMV: CSR segments staged in shared memory (tile_rows), Y written with streaming stores.
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads, ENS_GSPMV_MIN_BLOCKS)
-    gspmv_kernel(MatView A, int32_t m, const typename Arith::T *__restrict__ X, typename Arith::T *__restrict__ Y,
-                 uint32_t native_mask) {
+__device__ __forceinline__ void gspmv_body(const MatView &A, int32_t m, const typename Arith::T *__restrict__ X,
+                                           typename Arith::T *__restrict__ Y, uint32_t native_mask) {
   using T = typename Arith::T;
   tile_rows<Arith, VEC, LANES>(A, m, X, native_mask,
                                [&](int64_t i, int32_t c, const T (&y)[VEC]) { store_vec_cs<T, VEC>(Y + i * m + c, y); });
+}
+
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    gspmv_kernel(MatView A, int32_t m, const typename Arith::T *__restrict__ X, typename Arith::T *__restrict__ Y,
+                 uint32_t native_mask) {
+  gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
+}
+
+// The split path with a register cap (at least 6 resident blocks per SM, 40 registers): the
+// gather-latency-bound loop needs resident warps more than registers (measured on GB300: 6 blocks
+// beat 5 by 1-10 % over m = 2..32; with a minimum of one block per SM the compiler took 125-140
+// registers and every launch ran at half speed).
+#ifndef ENS_SPLIT_MIN_BLOCKS
+#define ENS_SPLIT_MIN_BLOCKS 6
+#endif
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads, ENS_SPLIT_MIN_BLOCKS)
+    gspmv_kernel_capped(MatView A, int32_t m, const typename Arith::T *__restrict__ X,
+                        typename Arith::T *__restrict__ Y, uint32_t native_mask) {
+  gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
 }
 
 int grid_for(const ens_matrix *A, const void *kernel) {
@@ -55,9 +74,13 @@ int grid_for(const ens_matrix *A, const void *kernel) {
 template <typename Arith, int VEC, int LANES>
 cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, cudaStream_t s) {
   using T = typename Arith::T;
-  auto k = gspmv_kernel<Arith, VEC, LANES>;
-  const int grid = grid_for(A, (const void *)k);
-  k<<<grid, kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
+  if constexpr (std::is_same<Arith, ArithF64Split>::value) {
+    auto k = gspmv_kernel_capped<Arith, VEC, LANES>;
+    k<<<grid_for(A, (const void *)k), kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
+  } else {
+    auto k = gspmv_kernel<Arith, VEC, LANES>;
+    k<<<grid_for(A, (const void *)k), kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
+  }
   return cudaGetLastError();
 }
 
