@@ -207,17 +207,118 @@ def solve_metrics(reps: int = 2):
                 "iters": st["iters"].tolist(),
                 "outer": st["outer"].tolist(),
             }
+        if pre == "chebyshev":  # the same solves with the aggregation multigrid V-cycle instead
+            t_setup = time.perf_counter()
+            levels = A.amg_setup()
+            t_setup = time.perf_counter() - t_setup
+            for prec in ("f64", "mixed"):
+                t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tol, precond="amg", precision=prec))
+                res[prec + "_amg"] = {
+                    "solves_per_s": m / t,
+                    "seconds": t,
+                    "max_relres": float(st["relres"].max()),
+                    "converged": int((st["status"] == 0).sum()),
+                    "iters": st["iters"].tolist(),
+                    "outer": st["outer"].tolist(),
+                }
+            res["amg_setup_s"] = t_setup
+            res["amg_levels"] = levels
         cols = [B[:, l : l + 1].contiguous() for l in range(m)]
         t1, outs = timed(lambda: [ens.solve_block(A, c, tol=tol, precond=pre, precision="f64") for c in cols])
         base = m / t1
         res["one_rhs_f64"] = {"solves_per_s": base, "seconds": t1, "iters": [int(o[1]["iters"][0]) for o in outs]}
-        for prec in ("f64", "mixed"):
-            res[prec]["speedup_vs_one_rhs_f64"] = res[prec]["solves_per_s"] / base
+        for prec in ("f64", "mixed", "f64_amg", "mixed_amg"):
+            if prec in res:
+                res[prec]["speedup_vs_one_rhs_f64"] = res[prec]["solves_per_s"] / base
         res["tol"] = tol
         res["precond"] = pre
         out[name] = res
         A.close()
     return out
+
+
+def cubes_gspmv_metrics(reps: int = 20):
+    """FP64 GSpMV on the wall-mounted-cube operator 192 x 128 x 96 (rows of 5-7 nonzeros) at m = 8,
+    autotuned: device time per launch (CUDA events, 3 warm-up launches) and algorithmic GB/s."""
+    import torch
+
+    import gen
+    import paper_1711_10622_gb300 as ens
+
+    op = gen.WORKLOADS["cubes192x128x96_m8"]["op"]()
+    m = 8
+    A = ens.Matrix.from_operator(op)
+    tuned = A.autotune(m, "f64")
+    X = torch.from_numpy(gen.rhs_normal(op.n, m, 20100)).cuda()
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        ens.gspmv(A, X, Y)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        ens.gspmv(A, X, Y)
+    e.record()
+    torch.cuda.synchronize()
+    us = s.elapsed_time(e) / reps * 1e3
+    A.close()
+    b = alg_bytes(op.n, op.nnz, m)
+    return {"workload": "cubes192x128x96", "m": m, "n": op.n, "nnz": op.nnz, "us": us, "alg_mb": b / 1e6, "gbs": b / (us * 1e-6) / 1e9, "tuned": tuned}
+
+
+def fp64_peak_ops(sm_mhz=None):
+    """FP64 pipe ceiling in operations per second: 2 DFMA/DADD/DMUL per clock per SM (the peak
+    the profiler reports for this part) x 152 SMs x the SM clock (sampled, else the 2070 MHz max)."""
+    mhz = sm_mhz or 2070.0
+    return 2.0 * 152 * mhz * 1e6
+
+
+def projection_metrics(m: int = 8, reps: int = 20):
+    """The projection step around the solve (Section 2.2, Eqs. eq2/eq3) on the 256 x 128 x 128
+    channel grid at m states: device time of ens_divergence and ens_grad_correct, their
+    algorithmic bytes (every face value, pressure and divergence touched once) and FP64 operation
+    counts. Inputs resident; every launch streams > 1 GB (> L2)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1711_10622_gb300 as ens
+
+    op = gen.channel(256, 128, 128)
+    g = gen.grid_of(op)
+    U, V, W = (torch.from_numpy(c).cuda() for c in gen.predictor_velocity(g, m, 400, noise=0.1))
+    P = torch.from_numpy(np.random.default_rng(9).standard_normal((op.n, m))).cuda()
+    G = ens.Grid.from_grid(g)
+    D = torch.empty(op.n, m, dtype=torch.float64, device="cuda")
+    faces = sum(G.nfaces)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps * 1e3
+
+    t_div = timed(lambda: ens.divergence(G, U, V, W, scale=-1.0, D=D))
+    t_cor = timed(lambda: ens.grad_correct(G, P, U, V, W, 1e-9))
+    G.close()
+    b_div = 8 * m * (faces + op.n) + op.n  # faces read, D written, open-face mask
+    b_cor = 8 * m * (2 * faces + op.n) + op.n  # faces read and written, P read, mask
+    ops_div = 7 * op.n * m  # 6 DFMA + 1 DMUL per cell and state
+    ops_cor = 9 * op.n * m  # per owned face: difference, scaling, update
+    return {
+        "workload": "channel256x128x128",
+        "m": m,
+        "divergence": {"us": t_div, "alg_bytes": b_div, "gbs": b_div / (t_div * 1e-6) / 1e9, "fp64_ops": ops_div,
+                       "fp64_gops": ops_div / (t_div * 1e-6) / 1e9},
+        "grad_correct": {"us": t_cor, "alg_bytes": b_cor, "gbs": b_cor / (t_cor * 1e-6) / 1e9, "fp64_ops": ops_cor,
+                         "fp64_gops": ops_cor / (t_cor * 1e-6) / 1e9},
+    }
 
 
 def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float = 120e9, slots: int = 4):
@@ -331,8 +432,9 @@ def run_reference(args):
 
 def run_profile(args):
     """Launch-only mode for ncu captures: W + K GSpMV launches per (m, arithmetic) on a channel
-    operator of the requested size, no timing output. Sizes: 'full' = 256 x 128 x 128, 'half' =
-    128 x 128 x 128 (inputs still larger than L2, a few GB on the device at most)."""
+    operator of the requested size, no timing output; with --profile-modes projection, W + K
+    divergence + correction pairs on that channel's grid instead. Sizes: 'full' = 256 x 128 x 128,
+    'half' = 128 x 128 x 128 (inputs still larger than L2, a few GB on the device at most)."""
     import torch
 
     import gen
@@ -343,9 +445,30 @@ def run_profile(args):
 
     dims = {"full": (256, 128, 128), "half": (128, 128, 128)}[args.profile_size]
     op = gen.channel(*dims)
-    A = ens.Matrix.from_operator(op)
     ms = [int(v) for v in args.profile_m.split(",")]
     modes = args.profile_modes.split(",")
+    if modes == ["projection"]:  # ens_divergence + ens_grad_correct, inside the NVTX range "profiled"
+        import numpy as np
+
+        g = gen.grid_of(op)
+        G = ens.Grid.from_grid(g)
+        for m in ms:
+            U, V, W = (torch.from_numpy(c).cuda() for c in gen.predictor_velocity(g, m, 400, noise=0.1))
+            P = torch.from_numpy(np.random.default_rng(9).standard_normal((op.n, m))).cuda()
+            D = torch.empty(op.n, m, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("profiled")
+            for _ in range(args.warmup + args.steps):
+                ens.divergence(G, U, V, W, scale=-1.0, D=D)
+                ens.grad_correct(G, P, U, V, W, 1e-9)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            del U, V, W, P, D
+            torch.cuda.empty_cache()
+        G.close()
+        print(json.dumps({"profile": "projection", "size": dims, "m": ms, "launches_per_case": 2 * (args.warmup + args.steps)}))
+        return 0
+    A = ens.Matrix.from_operator(op)
     for m in ms:
         X = torch.from_numpy(gen.rhs_normal(op.n, m, 20000 + m)).to("cuda")
         for mode in modes:
@@ -515,10 +638,12 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.25)
+    torch.cuda.nvtx.range_push("timed")  # the launch-list capture selects these launches
     start.record(stream)
     for k in range(K):
         step(evs[k])
     end.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -588,6 +713,16 @@ def main():
     }
 
     solves = None if args.no_solves else solve_metrics()
+    projection = None if args.no_solves else projection_metrics()
+    cubes = None if args.no_solves else cubes_gspmv_metrics()
+    if cubes is not None:
+        cubes["frac_of_measured_peak"] = cubes["gbs"] / peak
+    if projection is not None:
+        ceiling = fp64_peak_ops(clocks.get("sm_mhz") if isinstance(clocks, dict) else None) / 1e9
+        for k in ("divergence", "grad_correct"):
+            projection[k]["fp64_frac"] = projection[k]["fp64_gops"] / ceiling
+            projection[k]["hbm_frac"] = projection[k]["gbs"] / peak
+        projection["fp64_ceiling_gops"] = ceiling
     serving = None if args.serving_requests <= 0 else serving_metrics(args.serving_requests)
     from paper_1711_10622_gb300 import report
 
@@ -623,6 +758,8 @@ def main():
             "sweep": sweep,
             "e2e": e2e,
             "solves": solves,
+            "projection": projection,
+            "cubes_gspmv": cubes,
             "serving": serving,
             "paper_estimate": estimate,
             "cpu_baseline": cpu,

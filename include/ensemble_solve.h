@@ -150,12 +150,13 @@ ens_status ens_gspmv_host_noalloc(const ens_matrix *A, int32_t m, int32_t dtype,
 
 /* ---------------------------------------------------------------- multi-RHS BiCGStab solve */
 
-typedef enum { ENS_PRECOND_NONE = 0, ENS_PRECOND_CHEBYSHEV = 1 } ens_precond;
+typedef enum { ENS_PRECOND_NONE = 0, ENS_PRECOND_CHEBYSHEV = 1, ENS_PRECOND_AMG = 2 } ens_precond;
 typedef enum { ENS_PREC_F64 = 0, ENS_PREC_MIXED = 1 } ens_precision;
 
 typedef struct {
   int32_t max_iter;    /* BiCGStab iterations per column (FP64 mode); default 10000 */
-  int32_t precond;     /* ENS_PRECOND_NONE (default) or ENS_PRECOND_CHEBYSHEV */
+  int32_t precond;     /* ENS_PRECOND_NONE (default), ENS_PRECOND_CHEBYSHEV, or ENS_PRECOND_AMG (one
+                          V-cycle of the hierarchy built by ens_amg_setup on the matrix) */
   int32_t cheb_steps;  /* Chebyshev updates per application, >= 1 (default 4 = 3 GSpMVs; polynomial
                           of degree cheb_steps - 1 in D^-1 A) */
   double cheb_lo;      /* eigenvalue interval [cheb_lo, cheb_hi] of D^-1 A, 0 < lo < hi */
@@ -225,6 +226,56 @@ typedef struct {
  * The items' buffers must not overlap. Synchronous. Errors name the offending item.
  */
 ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_solve_opts *opts, void *stream);
+
+/*
+ * Aggregation multigrid preconditioner ("AMG-lite"). The paper's solver is BiCGStab with algebraic
+ * multigrid (Section 4.1); this is a lighter stand-in built once per matrix:
+ *   strength   j != i is a strong neighbour of i when |a_ij| >= theta sqrt(|a_ii| |a_jj|);
+ *   aggregates plain aggregation in three greedy phases (Vanek, Mandel, Brezina 1996): rows in
+ *              increasing order start an aggregate with their strong neighbours when all of them
+ *              are free; left-over rows join the phase-1 aggregate of their strongest aggregated
+ *              strong neighbour (largest |a_ij|, then the smallest j); rows still free start
+ *              aggregates with their free strong neighbours;
+ *   transfer   piecewise constant P, restriction P^T; coarse operators A_c = P^T A P;
+ *   levels     coarsen while n > coarse_size (at most max_levels, each level <= n / 1.5 rows);
+ *   V-cycle    z = S(r); z += P V(P^T (r - A z)); z += S(r - A z), S = the Jacobi-scaled Chebyshev
+ *              iteration on the level's matrix (smooth_steps updates, interval [cheb_lo, cheb_hi]
+ *              of D^-1 A_l); the coarsest level runs coarse_steps Chebyshev updates.
+ * The V-cycle is one fixed linear operator, applied to all m columns of a block at once (every
+ * level's products are GSpMVs); ens_solve_block with ENS_PRECOND_AMG uses it as M^-1.
+ */
+typedef struct {
+  double theta;          /* strength threshold (default 0.08) */
+  int32_t max_levels;    /* levels including the fine one, 2..16 (default 8) */
+  int32_t coarse_size;   /* stop coarsening at or below this many rows (default 512) */
+  int32_t smooth_steps;  /* Chebyshev updates per smoothing, >= 1 (default 2 = 1 GSpMV) */
+  int32_t coarse_steps;  /* Chebyshev updates on the coarsest level, >= 1 (default 16) */
+  double cheb_lo;        /* smoother interval of D^-1 A_l (default [2/30, 2]: diagonal dominance */
+  double cheb_hi;        /* is kept by P^T A P, so 2 bounds every level) */
+} ens_amg_opts;
+
+/* Fill *o with the defaults listed above. */
+void ens_default_amg_opts(ens_amg_opts *o);
+
+/* Build the hierarchy of A and attach it (replacing any previous one). Reads A back to the host,
+ * aggregates and forms the coarse operators there, and uploads them as matrices of their own.
+ * opts may be NULL (defaults). Synchronises `stream`. ENS_ERR_INVALID for bad options; on a
+ * device error nothing is attached. Not concurrent with other calls on A. */
+ens_status ens_amg_setup(ens_matrix *A, const ens_amg_opts *opts, void *stream);
+
+/* Level count of A's hierarchy (0 if none) and, if the arrays are not NULL, the rows and nonzeros
+ * of each level (host arrays of at least that many entries). */
+ens_status ens_amg_info(const ens_matrix *A, int32_t *levels, int64_t *rows, int64_t *nnz);
+
+/* Host copies of level `level`: its CSR (row_ptr [rows+1], col_idx and val [nnz]) and, except on the
+ * coarsest level, agg [rows] (next-level row of each row). Any pointer may be NULL. Synchronous. */
+ens_status ens_amg_level(const ens_matrix *A, int32_t level, int32_t *row_ptr, int32_t *col_idx, double *val,
+                         int32_t *agg);
+
+/* Z = V(R): one V-cycle on an n x m row-interleaved DEVICE block (dtype ENS_F64 or ENS_F32; the
+ * float32 cycle uses the float32 copies of every level), 1 <= m <= 64. Workspace is allocated
+ * stream-ordered for the call. Synchronous. ENS_ERR_INVALID without a hierarchy. */
+ens_status ens_amg_apply(const ens_matrix *A, int32_t m, int32_t dtype, const void *R, void *Z, void *stream);
 
 /* Human-readable message of the last failed call on this host thread ("" if none). */
 const char *ens_last_error(void);

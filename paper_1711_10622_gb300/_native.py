@@ -32,7 +32,7 @@ _i64 = ctypes.c_int64
 _u32 = ctypes.c_uint32
 
 
-ENS_PRECOND_NONE, ENS_PRECOND_CHEBYSHEV = 0, 1
+ENS_PRECOND_NONE, ENS_PRECOND_CHEBYSHEV, ENS_PRECOND_AMG = 0, 1, 2
 ENS_PREC_F64, ENS_PREC_MIXED = 0, 1
 
 
@@ -52,6 +52,20 @@ class SolveOpts(ctypes.Structure):
         ("check_every", ctypes.c_int32),
         ("x0_zero", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
+    ]
+
+
+class AmgOpts(ctypes.Structure):
+    """Mirror of ens_amg_opts."""
+
+    _fields_ = [
+        ("theta", ctypes.c_double),
+        ("max_levels", ctypes.c_int32),
+        ("coarse_size", ctypes.c_int32),
+        ("smooth_steps", ctypes.c_int32),
+        ("coarse_steps", ctypes.c_int32),
+        ("cheb_lo", ctypes.c_double),
+        ("cheb_hi", ctypes.c_double),
     ]
 
 
@@ -129,6 +143,11 @@ def lib():
         "ens_grid_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
         "ens_divergence": (_i32, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]),
         "ens_grad_correct": (_i32, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]),
+        "ens_default_amg_opts": (None, [ctypes.POINTER(AmgOpts)]),
+        "ens_amg_setup": (_i32, [_vp, ctypes.POINTER(AmgOpts), _vp]),
+        "ens_amg_info": (_i32, [_vp, ctypes.POINTER(_i32), _vp, _vp]),
+        "ens_amg_level": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
+        "ens_amg_apply": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_last_error": (ctypes.c_char_p, []),
         "ens_version": (ctypes.c_char_p, []),
     }

@@ -95,6 +95,37 @@ class Matrix:
         )
         return {"m": int(m), "dtype": dtype, "lanes": lanes.value, "share": share.value, "best_us": us.value}
 
+    def amg_setup(self, stream=None, **opts):
+        """Build the aggregation multigrid hierarchy (ens_amg_setup); keyword overrides of
+        ens_amg_opts: theta, max_levels, coarse_size, smooth_steps, coarse_steps, cheb_lo, cheb_hi."""
+        o = N.AmgOpts()
+        N.lib().ens_default_amg_opts(ctypes.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        N.check(N.lib().ens_amg_setup(self.handle, ctypes.byref(o), _stream_handle(stream)))
+        return self.amg_info()
+
+    def amg_info(self) -> list:
+        """[(rows, nnz)] per level of the hierarchy ([] without one)."""
+        nl = ctypes.c_int32()
+        N.check(N.lib().ens_amg_info(self.handle, ctypes.byref(nl), None, None))
+        rows = np.zeros(max(nl.value, 1), dtype=np.int64)
+        nnz = np.zeros(max(nl.value, 1), dtype=np.int64)
+        N.check(N.lib().ens_amg_info(self.handle, ctypes.byref(nl), rows.ctypes.data_as(ctypes.c_void_p), nnz.ctypes.data_as(ctypes.c_void_p)))
+        return [(int(rows[l]), int(nnz[l])) for l in range(nl.value)]
+
+    def amg_level(self, level: int):
+        """(row_ptr, col_idx, val, agg) of one hierarchy level (agg None on the coarsest)."""
+        info = self.amg_info()
+        nl, nz = info[level]
+        row = np.zeros(nl + 1, dtype=np.int32)
+        col = np.zeros(max(nz, 1), dtype=np.int32)
+        val = np.zeros(max(nz, 1))
+        agg = np.zeros(nl, dtype=np.int32) if level < len(info) - 1 else None
+        vp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        N.check(N.lib().ens_amg_level(self.handle, int(level), vp(row), vp(col), vp(val), vp(agg)))
+        return row, col[:nz], val[:nz], agg
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             N.check(N.lib().ens_destroy_matrix(self._h))
@@ -162,16 +193,30 @@ def gspmv_host(A: Matrix, X: np.ndarray, Y: np.ndarray | None = None, stream=Non
 COL_STATUS = {0: "converged", 1: "maxiter", 2: "breakdown", 3: "nonfinite", 4: "incompatible"}
 
 
+def amg_apply(A: Matrix, R, Z=None, stream=None):
+    """Z = V(R): one V-cycle of A's hierarchy on an (n, m) float64/float32 CUDA block (ens_amg_apply)."""
+    import torch
+
+    _check_block(A, R, "R")
+    if Z is None:
+        Z = torch.empty_like(R)
+    _check_block(A, Z, "Z")
+    N.check(
+        N.lib().ens_amg_apply(A.handle, R.shape[1], _dtype_code(R), ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()), _stream_handle(stream))
+    )
+    return Z
+
+
 def solve_opts(**kw) -> N.SolveOpts:
     """ens_solve_opts with the library defaults, overridden by keyword (precond / precision may be
-    given by name: 'none' | 'chebyshev', 'f64' | 'mixed')."""
+    given by name: 'none' | 'chebyshev' | 'amg', 'f64' | 'mixed')."""
     o = N.SolveOpts()
     N.lib().ens_default_solve_opts(ctypes.byref(o))
     for k, v in kw.items():
         if v is None:
             continue
         if k == "precond":
-            v = {"none": N.ENS_PRECOND_NONE, "chebyshev": N.ENS_PRECOND_CHEBYSHEV}.get(v, v)
+            v = {"none": N.ENS_PRECOND_NONE, "chebyshev": N.ENS_PRECOND_CHEBYSHEV, "amg": N.ENS_PRECOND_AMG}.get(v, v)
         if k == "precision":
             v = {"f64": N.ENS_PREC_F64, "mixed": N.ENS_PREC_MIXED}.get(v, v)
         if k == "x0_zero":

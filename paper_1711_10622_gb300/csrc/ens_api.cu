@@ -72,6 +72,7 @@ cudaError_t dmalloc(T **p, size_t count) {
 }
 
 void free_matrix(ens_matrix *A) {
+  free_amg(A->amg);
   cudaFree(A->row);
   cudaFree(A->col);
   cudaFree(A->val);

@@ -5,8 +5,11 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "ensemble_solve.h"
+
+struct ens_amg;  // aggregation multigrid hierarchy attached to a matrix (amg.cu)
 
 constexpr int kTuneMaxM = 64;  // block widths the autotuner keeps a choice for
 constexpr int kShareHybrid = 64;  // "native share" code of the column-hybrid FP64 arithmetic
@@ -40,9 +43,29 @@ struct ens_matrix {
   // solver workspace (grown on demand)
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  // aggregation multigrid hierarchy (ens_amg_setup), owned
+  ens_amg *amg = nullptr;
+};
+
+// One level of the aggregation hierarchy: its matrix (level 0 borrows the fine matrix) and, on
+// every level but the coarsest, the map to the next level's rows.
+struct ens_amg_lev {
+  ens_matrix *A = nullptr;
+  bool owned = false;
+  int64_t nc = 0;               // rows of the next level
+  int32_t *agg = nullptr;       // [n] aggregate (next-level row) of each row
+  int32_t *agg_ptr = nullptr;   // [nc + 1] start of each aggregate in members
+  int32_t *members = nullptr;   // [n] rows grouped by aggregate, ascending within each
+};
+struct ens_amg {
+  ens_amg_opts opts;
+  std::vector<ens_amg_lev> lev;
 };
 
 namespace ens {
+
+// Release a hierarchy (coarse matrices and maps; not the fine matrix).
+void free_amg(ens_amg *H);
 
 // Record a formatted message for ens_last_error() and return `st`.
 ens_status fail(ens_status st, const char *fmt, ...);

@@ -48,8 +48,12 @@ ens_status validate_solve(const ens_matrix *A, int32_t m, const double *B, doubl
       return fail(ENS_ERR_INVALID, "solve_block: tol[%d] must be finite and >= 0", l);
   if ((uintptr_t)B % 8 || (uintptr_t)X % 8) return fail(ENS_ERR_INVALID, "solve_block: B/X not 8-byte aligned");
   if (o.max_iter < 0) return fail(ENS_ERR_INVALID, "solve_block: max_iter < 0");
-  if (o.precond != ENS_PRECOND_NONE && o.precond != ENS_PRECOND_CHEBYSHEV)
+  if (o.precond != ENS_PRECOND_NONE && o.precond != ENS_PRECOND_CHEBYSHEV && o.precond != ENS_PRECOND_AMG)
     return fail(ENS_ERR_INVALID, "solve_block: unknown preconditioner %d", o.precond);
+  if (o.precond == ENS_PRECOND_AMG) {
+    if (!A->amg) return fail(ENS_ERR_INVALID, "solve_block: ENS_PRECOND_AMG needs ens_amg_setup on the matrix");
+    if (!A->full_diag) return fail(ENS_ERR_INVALID, "solve_block: AMG smoothing needs a nonzero diagonal in every row");
+  }
   if (o.precond == ENS_PRECOND_CHEBYSHEV) {
     if (o.cheb_steps < 1 || o.cheb_steps > 64) return fail(ENS_ERR_INVALID, "solve_block: cheb_steps outside [1, 64]");
     if (!(o.cheb_lo > 0.0) || !(o.cheb_hi > o.cheb_lo) || !std::isfinite(o.cheb_hi))
@@ -170,3 +174,79 @@ ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, doub
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- AMG apply
+namespace ens {
+namespace {
+
+template <typename T>
+__global__ void k_amg_pad(int64_t n, int32_t m, int32_t mp, const T *__restrict__ src, T *__restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * mp; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / mp;
+    const int32_t l = (int32_t)(t - i * mp);
+    dst[t] = l < m ? src[i * m + l] : T(0);
+  }
+}
+template <typename T>
+__global__ void k_amg_unpad(int64_t n, int32_t m, int32_t mp, const T *__restrict__ src, T *__restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * m; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / m;
+    dst[t] = src[i * mp + (t - i * m)];
+  }
+}
+
+template <typename Arith>
+ens_status amg_apply_impl(const ens_matrix *A, int32_t m, const void *R, void *Z, cudaStream_t s) {
+  using T = typename Arith::T;
+  const int32_t mp = m == 1 ? 1 : (m + 1) & ~1;
+  const int vec = mp == 1 ? 1 : 2;
+  int lanes = 1;
+  while (lanes * vec < mp) lanes <<= 1;
+  const int64_t n = A->n;
+  cudaError_t e = cudaSuccess;
+  {
+    solver::Scratch sc(s);
+    const T *r = (const T *)R;
+    T *z = (T *)Z;
+    T *rp = nullptr, *zp = nullptr;
+    const int pgrid = (int)std::max<int64_t>(1, std::min<int64_t>((n * mp + 255) / 256, (int64_t)A->num_sms * 8));
+    if (mp != m) {
+      e = sc.get(&rp, (size_t)n * mp);
+      if (e == cudaSuccess) e = sc.get(&zp, (size_t)n * mp);
+      if (e == cudaSuccess) {
+        k_amg_pad<T><<<pgrid, 256, 0, s>>>(n, m, mp, r, rp);
+        e = cudaGetLastError();
+      }
+      r = rp;
+    }
+    solver::AmgCycle<Arith> cyc;
+    if (e == cudaSuccess) e = cyc.setup(sc, A->amg, mp, vec, lanes);
+    if (e == cudaSuccess) e = cyc.apply(r, mp != m ? zp : z, s);
+    if (e == cudaSuccess && mp != m) {
+      k_amg_unpad<T><<<pgrid, 256, 0, s>>>(n, m, mp, zp, z);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "amg_apply");
+  return ENS_OK;
+}
+
+}  // namespace
+}  // namespace ens
+
+extern "C" ens_status ens_amg_apply(const ens_matrix *A, int32_t m, int32_t dtype, const void *R, void *Z, void *stream) {
+  clear_error();
+  if (!A || !A->amg) return fail(ENS_ERR_INVALID, "amg_apply: matrix has no hierarchy (ens_amg_setup)");
+  if (m < 1 || m > kMaxSolveM) return fail(ENS_ERR_INVALID, "amg_apply: m = %d outside [1, %d]", m, kMaxSolveM);
+  if (!R || !Z) return fail(ENS_ERR_INVALID, "amg_apply: R or Z is NULL");
+  if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "amg_apply: unknown dtype %d", dtype);
+  if (!A->full_diag) return fail(ENS_ERR_INVALID, "amg_apply: smoothing needs a nonzero diagonal in every row");
+  const size_t es = dtype == ENS_F64 ? 8 : 4;
+  const uintptr_t r = (uintptr_t)R, z = (uintptr_t)Z, bytes = (uintptr_t)A->n * m * es;
+  if (r < z + bytes && z < r + bytes) return fail(ENS_ERR_INVALID, "amg_apply: R and Z overlap");
+  if (r % (2 * es) || z % (2 * es)) return fail(ENS_ERR_INVALID, "amg_apply: R/Z must be %zu-byte aligned", 2 * es);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == ENS_F32) return amg_apply_impl<ArithF32>(A, m, R, Z, s);
+  return use_split(A) ? amg_apply_impl<ArithF64Split>(A, m, R, Z, s) : amg_apply_impl<ArithF64Native>(A, m, R, Z, s);
+}

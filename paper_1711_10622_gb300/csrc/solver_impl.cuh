@@ -611,6 +611,208 @@ cudaError_t alloc_cols(Scratch &sc, int m, Cols<T> &cs) {
 
 // One BiCGStab run over an mp-wide internal block in arithmetic Arith (float64 split/native or
 // float32). b, x are device blocks of stride mp.
+// ----------------------------------------------------------------------------- AMG V-cycle
+// One V-cycle of the aggregation hierarchy (amg.cu) on an mp-wide block, every level's product a
+// GSpMV of that level's matrix over the whole block:
+//   z = S(r);  z += P V(P^T (r - A z));  z += S(r - A z);   coarsest level: z = S_coarse(r)
+// with S the Jacobi-scaled Chebyshev iteration (first term below, further steps by k_cheb).
+
+// d0 = D^-1 src / theta; z = d0 (or z += d0 for the post-smoothing).
+template <typename Arith, int VEC, int LANES, bool ADD>
+__global__ void __launch_bounds__(kThreads)
+    k_amg_first(MatView A, int32_t m, const typename Arith::T *__restrict__ src, typename Arith::T *__restrict__ da,
+                typename Arith::T *z, typename Arith::T inv_theta) {
+  using T = typename Arith::T;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  ENS_ROWS(i) {
+    T sv[VEC], zv[VEC];
+    load_vec<T, VEC>(src + i * m + c, sv);
+    const T sc = Arith::dinv(A, i) * inv_theta;
+    if (ADD) load_vec_rw<T, VEC>(z + i * m + c, zv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      sv[q] *= sc;
+      zv[q] = ADD ? zv[q] + sv[q] : sv[q];
+    }
+    store_vec<T, VEC>(da + i * m + c, sv);
+    store_vec<T, VEC>(z + i * m + c, zv);
+  }
+}
+
+// res = r - A z
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_amg_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ z, const typename Arith::T *__restrict__ r,
+                typename Arith::T *__restrict__ res, uint32_t mask) {
+  using T = typename Arith::T;
+  tile_rows<Arith, VEC, LANES>(A, m, z, mask, [&](int64_t i, int32_t cc, const T (&w)[VEC]) {
+    T rv[VEC];
+    load_vec<T, VEC>(r + i * m + cc, rv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) rv[q] -= w[q];
+    store_vec<T, VEC>(res + i * m + cc, rv);
+  });
+}
+
+// rc_I = sum of res_i over the rows i of aggregate I (ascending rows: a fixed order).
+template <typename T, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_amg_restrict(int64_t nc, int32_t m, const int32_t *__restrict__ ptr, const int32_t *__restrict__ mem,
+                   const T *__restrict__ res, T *__restrict__ rc) {
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  for (int64_t I = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; I < nc;
+       I += (int64_t)gridDim.x * (kThreads / LANES)) {
+    T acc[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) acc[q] = T(0);
+    for (int32_t t = ptr[I]; t < ptr[I + 1]; ++t) {
+      T v[VEC];
+      load_vec<T, VEC>(res + (int64_t)mem[t] * m + c, v);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[q] += v[q];
+    }
+    store_vec<T, VEC>(rc + I * m + c, acc);
+  }
+}
+
+// z_i += zc_agg(i)
+template <typename T, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_amg_prolong(int64_t n, int32_t m, const int32_t *__restrict__ agg, const T *__restrict__ zc, T *z) {
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  if (c >= m) return;
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < n;
+       i += (int64_t)gridDim.x * (kThreads / LANES)) {
+    T zv[VEC], cv[VEC];
+    load_vec_rw<T, VEC>(z + i * m + c, zv);
+    load_vec<T, VEC>(zc + (int64_t)agg[i] * m + c, cv);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) zv[q] += cv[q];
+    store_vec<T, VEC>(z + i * m + c, zv);
+  }
+}
+
+template <typename Arith>
+struct AmgCycle {
+  using T = typename Arith::T;
+  struct Level {
+    MatView A;
+    int64_t n = 0, nc = 0;
+    const int32_t *agg = nullptr, *ptr = nullptr, *mem = nullptr;
+    uint32_t mask = 0;
+    bool split = false;  // float64 split arithmetic usable on this level
+    int grid = 0, egrid = 0, cgrid = 0;
+    T *r = nullptr, *z = nullptr, *res = nullptr, *cres = nullptr, *da = nullptr, *db = nullptr;
+  };
+  std::vector<Level> lev;
+  ens_amg_opts o;
+  int mp = 0, vec = 2, lanes = 1;
+
+  cudaError_t setup(Scratch &sc, const ens_amg *H, int mp_, int vec_, int lanes_) {
+    o = H->opts;
+    mp = mp_;
+    vec = vec_;
+    lanes = lanes_;
+    lev.clear();
+    cudaError_t e = cudaSuccess;
+    for (size_t l = 0; l < H->lev.size() && e == cudaSuccess; ++l) {
+      const ens_amg_lev &h = H->lev[l];
+      Level L;
+      L.A = view_of(h.A);
+      L.n = h.A->n;
+      L.nc = h.nc;
+      L.agg = h.agg;
+      L.ptr = h.agg_ptr;
+      L.mem = h.members;
+      L.split = use_split(h.A);
+      L.mask = std::is_same<Arith, ArithF64Split>::value && L.split ? share_mask(native_share(h.A, mp)) : 0u;
+      const int64_t rows_per_block = kThreads / lanes;
+      const int64_t sms = h.A->num_sms;
+      L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + kTileRows - 1) / kTileRows, sms * 4));
+      L.egrid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + rows_per_block - 1) / rows_per_block, sms * 8));
+      L.cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((L.nc + rows_per_block - 1) / rows_per_block, sms * 8));
+      const size_t blk = (size_t)L.n * mp;
+      if (l > 0) {
+        if (e == cudaSuccess) e = sc.get(&L.r, blk);
+        if (e == cudaSuccess) e = sc.get(&L.z, blk);
+      }
+      T **bufs[] = {&L.res, &L.cres, &L.da, &L.db};
+      for (T **b : bufs)
+        if (e == cudaSuccess) e = sc.get(b, blk);
+      lev.push_back(L);
+    }
+    return e;
+  }
+
+  // z (+)= S(src) on level l with `steps` Chebyshev updates, level arithmetic Ar.
+  template <typename Ar, int V, int Ln>
+  void smooth(const Level &L, const T *src, T *z, bool add, int steps, cudaStream_t st) {
+    const double theta = 0.5 * (o.cheb_hi + o.cheb_lo), delta = 0.5 * (o.cheb_hi - o.cheb_lo);
+    if (add)
+      k_amg_first<Ar, V, Ln, true><<<L.egrid, kThreads, 0, st>>>(L.A, mp, src, L.da, z, (T)(1.0 / theta));
+    else
+      k_amg_first<Ar, V, Ln, false><<<L.egrid, kThreads, 0, st>>>(L.A, mp, src, L.da, z, (T)(1.0 / theta));
+    const double sigma = theta / delta;
+    double rho_prev = 1.0 / sigma;
+    T *din = L.da, *dout = L.db;
+    for (int k = 1; k < steps; ++k) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta);
+      const bool first = k == 1, last = k == steps - 1;
+      if (first && last)
+        k_cheb<Ar, V, Ln, true, true><<<L.grid, kThreads, 0, st>>>(L.A, mp, din, dout, src, L.cres, z, c1, c2, L.mask);
+      else if (first)
+        k_cheb<Ar, V, Ln, true, false><<<L.grid, kThreads, 0, st>>>(L.A, mp, din, dout, src, L.cres, z, c1, c2, L.mask);
+      else if (last)
+        k_cheb<Ar, V, Ln, false, true><<<L.grid, kThreads, 0, st>>>(L.A, mp, din, dout, src, L.cres, z, c1, c2, L.mask);
+      else
+        k_cheb<Ar, V, Ln, false, false><<<L.grid, kThreads, 0, st>>>(L.A, mp, din, dout, src, L.cres, z, c1, c2, L.mask);
+      std::swap(din, dout);
+      rho_prev = rho;
+    }
+  }
+
+  template <typename Ar, int V, int Ln>
+  void level_cycle(size_t l, const T *r, T *z, cudaStream_t st) {
+    const Level &L = lev[l];
+    if (l + 1 == lev.size()) {
+      this->template smooth<Ar, V, Ln>(L, r, z, false, o.coarse_steps, st);
+      return;
+    }
+    const Level &C = lev[l + 1];
+    this->template smooth<Ar, V, Ln>(L, r, z, false, o.smooth_steps, st);
+    k_amg_resid<Ar, V, Ln><<<L.grid, kThreads, 0, st>>>(L.A, mp, z, r, L.res, L.mask);
+    k_amg_restrict<T, V, Ln><<<L.cgrid, kThreads, 0, st>>>(L.nc, mp, L.ptr, L.mem, L.res, C.r);
+    this->template cycle<V, Ln>(l + 1, C.r, C.z, st);
+    k_amg_prolong<T, V, Ln><<<L.egrid, kThreads, 0, st>>>(L.n, mp, L.agg, C.z, z);
+    k_amg_resid<Ar, V, Ln><<<L.grid, kThreads, 0, st>>>(L.A, mp, z, r, L.res, L.mask);
+    this->template smooth<Ar, V, Ln>(L, L.res, z, true, o.smooth_steps, st);
+  }
+
+  // Levels where the split arithmetic cannot run (value range) use native DFMA.
+  template <int V, int Ln>
+  void cycle(size_t l, const T *r, T *z, cudaStream_t st) {
+    if constexpr (std::is_same<Arith, ArithF64Split>::value || std::is_same<Arith, ArithF64Hybrid>::value) {
+      if (!lev[l].split) {
+        this->template level_cycle<ArithF64Native, V, Ln>(l, r, z, st);
+        return;
+      }
+    }
+    this->template level_cycle<Arith, V, Ln>(l, r, z, st);
+  }
+
+  // z = V(r) on the fine level (capturable: kernel launches only).
+  cudaError_t apply(const T *r, T *z, cudaStream_t st) {
+    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+      constexpr int V = decltype(Vc)::value, Ln = decltype(Lc)::value;
+      this->template cycle<V, Ln>(0, r, z, st);
+      return cudaGetLastError();
+    });
+  }
+};
+
 template <typename Arith>
 struct Bicg {
   using T = typename Arith::T;
@@ -618,6 +820,8 @@ struct Bicg {
   int64_t n = 0;
   int mp = 0, vec = 2, lanes = 1, grid = 0;
   bool prec = false;
+  bool use_amg = false;
+  AmgCycle<Arith> amg;
   int cheb_steps = 4;
   uint32_t mask = 0;  // native-DFMA sweeps of the split arithmetic (hybrid tiles)
   double theta = 1, delta = 1;
@@ -654,11 +858,16 @@ struct Bicg {
       for (T **b : bufs)
         if (e == cudaSuccess) e = sc.get(b, blk);
     }
+    use_amg = !outer_only && o.precond == ENS_PRECOND_AMG && M->amg != nullptr;
     if (outer_only) {
     } else if (prec) {
       T **pb[] = {&ph, &sh, &da, &db, &res};
       for (T **b : pb)
         if (e == cudaSuccess) e = sc.get(b, blk);
+    } else if (use_amg) {
+      if (e == cudaSuccess) e = sc.get(&ph, blk);
+      if (e == cudaSuccess) e = sc.get(&sh, blk);
+      if (e == cudaSuccess) e = amg.setup(sc, M->amg, mp, vec, lanes);
     } else {
       ph = p;
       sh = s_;
@@ -731,6 +940,7 @@ struct Bicg {
         cheb<V, L>(p, ph, st);
       } else {
         k_p<Arith, V, L, false><<<grid, kThreads, 0, st>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
+        if (use_amg) amg.template cycle<V, L>(0, p, ph, st);
       }
       k_v<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, ph, v, rh, cs, partials, counter, mask);
       if (prec) {
@@ -738,6 +948,7 @@ struct Bicg {
         cheb<V, L>(s_, sh, st);
       } else {
         k_s<Arith, V, L, false><<<grid, kThreads, 0, st>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
+        if (use_amg) amg.template cycle<V, L>(0, s_, sh, st);
       }
       k_t<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, sh, t, s_, cs, partials, counter, mask);
       k_xr<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, ph, sh, s_, t, r, rh, max_iter, cs, partials, counter);
