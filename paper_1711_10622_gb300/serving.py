@@ -113,6 +113,8 @@ class Server:
 
     solve_fn(op_name, B_device, tol, stream) -> (X_device, stats) may replace the library call (tests
     of the host logic); by default it is paper_1711_10622_gb300.solve_block on the op's Matrix.
+    precond: 'chebyshev', 'none' or 'amg' (the aggregation hierarchy of every operator is built when
+    the server starts and counted in the resident memory).
     """
 
     def __init__(
@@ -134,9 +136,13 @@ class Server:
             from .api import Matrix
 
             for name, op in operators.items():
-                self.mats[name] = Matrix.from_operator(op)
-                # matrix copies held by the library: row_ptr, col, f64/f32/split values, inverse diagonals
-                resident += 4 * (op.n + 1) + op.nnz * (4 + 8 + 4 + 8) + 12 * op.n
+                A = Matrix.from_operator(op)
+                self.mats[name] = A
+                levels = A.amg_setup() if precond == "amg" else [(op.n, op.nnz)]
+                # matrix copies held by the library per level (the fine one and, with AMG, the coarse
+                # ones): row_ptr, col, f64/f32/split values, inverse diagonals, aggregate maps
+                for n_l, nnz_l in levels:
+                    resident += 4 * (n_l + 1) + nnz_l * (4 + 8 + 4 + 8) + 12 * n_l + (8 * n_l if precond == "amg" else 0)
         self.solve_fn = solve_fn or self._library_solve
         self.sched = Scheduler({k: op.n for k, op in operators.items()}, resident, budget_bytes, max_cols, precision)
         self.cv = threading.Condition()

@@ -26,7 +26,8 @@ def ens():
     return ens
 
 
-def test_alone_vs_in_the_mix_with_overlap(ens):
+@pytest.mark.parametrize("precond", ["chebyshev", "amg"])
+def test_alone_vs_in_the_mix_with_overlap(ens, precond):
     from paper_1711_10622_gb300.serving import Request, Server, latency_summary
 
     ops = {"cubes": gen.cubes(48, 32, 24, size=4), "chan": gen.channel(32, 24, 16), "box": gen.dirichlet_box(16)}
@@ -36,7 +37,7 @@ def test_alone_vs_in_the_mix_with_overlap(ens):
         return gen.rhs_normal(ops[name].n, m, seed, zero_mean=ops[name].singular)
 
     target = rhs("cubes", 3, 1)
-    with Server(ops, budget_bytes=16e9, slots=3, max_cols=16) as srv:
+    with Server(ops, budget_bytes=16e9, slots=3, max_cols=16, precond=precond) as srv:
         alone = srv.submit(Request("cubes", target.copy(), tol))
         assert alone.done.wait(120) and alone.error is None
         mix = [
