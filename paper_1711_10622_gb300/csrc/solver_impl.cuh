@@ -65,10 +65,24 @@ struct Tiny<float> {
   for (int64_t i = (int64_t)blockIdx.x * (kThreads / LANES) + threadIdx.x / LANES; i < A.n; \
        i += (int64_t)gridDim.x * (kThreads / LANES))
 
+// Kernels whose body is a GSpMV (tile_rows) are launched with a register cap of kTileMinBlocks
+// resident blocks per SM and a grid of that many blocks per SM: without it the split kernels took
+// 60 registers and 4 blocks per SM and ran their gathers at a lower occupancy than the standalone
+// GSpMV (the hybrid tile's shared memory allows 5).
+template <typename Arith>
+struct TileBlocks {
+  static constexpr int value = 6;
+};
+template <>
+struct TileBlocks<ArithF64Hybrid> {
+  static constexpr int value = 5;
+};
+#define ENS_TILE_BOUNDS(Arith) __launch_bounds__(kThreads, TileBlocks<Arith>::value)
+
 // ----------------------------------------------------------------------------- start
 // r = b - A x (or r = b and x = 0 when x0_zero), rhat = r; per column ||b||^2, ||r||^2, sum(b).
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void ENS_TILE_BOUNDS(Arith)
     k_start(MatView A, int32_t m, const typename Arith::T *__restrict__ b, typename Arith::T *x,
             typename Arith::T *__restrict__ r, typename Arith::T *__restrict__ rh, int x0_zero, int singular,
             typename Arith::T incompat, Cols<typename Arith::T> cs, typename Arith::T *partials,
@@ -188,7 +202,7 @@ __global__ void __launch_bounds__(kThreads)
 // din is the GSpMV input (read by neighbouring rows), so d_k goes to a second buffer. The last
 // step needs neither res_k nor d_k afterwards.
 template <typename Arith, int VEC, int LANES, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(kThreads)
+__global__ void ENS_TILE_BOUNDS(Arith)
     k_cheb(MatView A, int32_t m, const typename Arith::T *__restrict__ din, typename Arith::T *__restrict__ dout,
            const typename Arith::T *__restrict__ src, typename Arith::T *res, typename Arith::T *z,
            typename Arith::T c1, typename Arith::T c2, uint32_t mask) {
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // ----------------------------------------------------------------------------- v = A ph
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void ENS_TILE_BOUNDS(Arith)
     k_v(MatView A, int32_t m, const typename Arith::T *__restrict__ ph, typename Arith::T *__restrict__ v,
         const typename Arith::T *__restrict__ rh, Cols<typename Arith::T> cs,
         typename Arith::T *partials, unsigned *counter, uint32_t mask) {
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // ----------------------------------------------------------------------------- t = A sh
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void ENS_TILE_BOUNDS(Arith)
     k_t(MatView A, int32_t m, const typename Arith::T *__restrict__ sh, typename Arith::T *__restrict__ t,
         const typename Arith::T *__restrict__ s, Cols<typename Arith::T> cs, typename Arith::T *partials,
         unsigned *counter, uint32_t mask) {
@@ -457,7 +471,7 @@ __global__ void __launch_bounds__(kThreads)
 // True residual ||b - A x||^2 per column -> relres. With `outer` set (mixed mode) the residual is
 // also stored in r and the outer convergence test runs on it.
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void ENS_TILE_BOUNDS(Arith)
     k_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ b, const typename Arith::T *__restrict__ x,
             typename Arith::T *__restrict__ r, int outer, Cols<typename Arith::T> cs, typename Arith::T *partials,
             unsigned *counter, uint32_t mask) {
@@ -642,7 +656,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // res = r - A z
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads)
+__global__ void ENS_TILE_BOUNDS(Arith)
     k_amg_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ z, const typename Arith::T *__restrict__ r,
                 typename Arith::T *__restrict__ res, uint32_t mask) {
   using T = typename Arith::T;
@@ -730,7 +744,7 @@ struct AmgCycle {
       L.mask = std::is_same<Arith, ArithF64Split>::value && L.split ? share_mask(native_share(h.A, mp)) : 0u;
       const int64_t rows_per_block = kThreads / lanes;
       const int64_t sms = h.A->num_sms;
-      L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + kTileRows - 1) / kTileRows, sms * 4));
+      L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + kTileRows - 1) / kTileRows, sms * TileBlocks<Arith>::value));
       L.egrid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + rows_per_block - 1) / rows_per_block, sms * 8));
       L.cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((L.nc + rows_per_block - 1) / rows_per_block, sms * 8));
       const size_t blk = (size_t)L.n * mp;
@@ -818,7 +832,7 @@ struct Bicg {
   using T = typename Arith::T;
   MatView A;
   int64_t n = 0;
-  int mp = 0, vec = 2, lanes = 1, grid = 0;
+  int mp = 0, vec = 2, lanes = 1, grid = 0, tgrid = 0;  // grid: streaming kernels, tgrid: GSpMV kernels
   bool prec = false;
   bool use_amg = false;
   AmgCycle<Arith> amg;
@@ -843,6 +857,7 @@ struct Bicg {
     lanes = 1;
     while (lanes * vec < mp) lanes <<= 1;
     grid = M->num_sms * 4;
+    tgrid = M->num_sms * TileBlocks<Arith>::value;
     prec = o.precond == ENS_PRECOND_CHEBYSHEV;
     cheb_steps = o.cheb_steps;
     theta = 0.5 * (o.cheb_hi + o.cheb_lo);
@@ -873,7 +888,7 @@ struct Bicg {
       sh = s_;
       da = db = res = nullptr;
     }
-    if (e == cudaSuccess) e = sc.get(&partials, (size_t)grid * 3 * kMaxSolveM);
+    if (e == cudaSuccess) e = sc.get(&partials, (size_t)std::max(grid, tgrid) * 3 * kMaxSolveM);
     if (e == cudaSuccess) e = sc.get(&counter, 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = alloc_cols(sc, mp, cs);
@@ -894,7 +909,7 @@ struct Bicg {
     const T incompat = (T)(1e-10 * std::sqrt((double)n));
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-      k_start<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
+      k_start<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
                                                       partials, counter, mask);
       return cudaGetLastError();
     });
@@ -917,13 +932,13 @@ struct Bicg {
       const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta);
       const bool first = k == 1, last = k == cheb_steps - 1;
       if (first && last)
-        k_cheb<Arith, V, L, true, true><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, true, true><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (first)
-        k_cheb<Arith, V, L, true, false><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, true, false><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (last)
-        k_cheb<Arith, V, L, false, true><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, false, true><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else
-        k_cheb<Arith, V, L, false, false><<<grid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, false, false><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       std::swap(din, dout);
       rho_prev = rho;
     }
@@ -942,7 +957,7 @@ struct Bicg {
         k_p<Arith, V, L, false><<<grid, kThreads, 0, st>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
         if (use_amg) amg.template cycle<V, L>(0, p, ph, st);
       }
-      k_v<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, ph, v, rh, cs, partials, counter, mask);
+      k_v<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, ph, v, rh, cs, partials, counter, mask);
       if (prec) {
         k_s<Arith, V, L, true><<<grid, kThreads, 0, st>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
         cheb<V, L>(s_, sh, st);
@@ -950,7 +965,7 @@ struct Bicg {
         k_s<Arith, V, L, false><<<grid, kThreads, 0, st>>>(A, mp, r, v, s_, da, sh, inv_theta, cs, partials, counter);
         if (use_amg) amg.template cycle<V, L>(0, s_, sh, st);
       }
-      k_t<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, sh, t, s_, cs, partials, counter, mask);
+      k_t<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, sh, t, s_, cs, partials, counter, mask);
       k_xr<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, ph, sh, s_, t, r, rh, max_iter, cs, partials, counter);
       return cudaGetLastError();
     });
@@ -1055,7 +1070,7 @@ struct Bicg {
         k_colsum<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, (T)(1.0 / (double)n), cs, partials, counter);
       }
       k_fix<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, singular, cs);
-      k_resid<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, b, x, nullptr, 0, cs, partials, counter, mask);
+      k_resid<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, b, x, nullptr, 0, cs, partials, counter, mask);
       return cudaGetLastError();
     });
   }
@@ -1064,7 +1079,7 @@ struct Bicg {
     if (!st) st = s;
     return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-      k_resid<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, b, x, r, 1, cs, partials, counter, mask);
+      k_resid<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, b, x, r, 1, cs, partials, counter, mask);
       return cudaGetLastError();
     });
   }
