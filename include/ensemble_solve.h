@@ -38,7 +38,7 @@ typedef enum {
   ENS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
   ENS_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
   ENS_ERR_BUDGET = 5,      /* the request does not fit the memory budget */
-  ENS_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+  ENS_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } ens_status;
 
 /* Per-column outcome of a solve; the numeric values are part of the ABI. */
