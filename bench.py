@@ -449,7 +449,9 @@ def run_reference(args):
 def run_profile(args):
     """Launch-only mode for ncu captures: W + K GSpMV launches per (m, arithmetic) on a channel
     operator of the requested size, no timing output; with --profile-modes projection, W + K
-    divergence + correction pairs on that channel's grid instead. Sizes: 'full' = 256 x 128 x 128,
+    divergence + correction pairs on that channel's grid instead; with solve-amg / solve-chebyshev,
+    K BiCGStab iterations of the cube workload (192 x 128 x 96, m = 8, host-driven loop) instead.
+    Sizes: 'full' = 256 x 128 x 128,
     'half' = 128 x 128 x 128 (inputs still larger than L2, a few GB on the device at most)."""
     import torch
 
@@ -463,6 +465,22 @@ def run_profile(args):
     op = gen.channel(*dims)
     ms = [int(v) for v in args.profile_m.split(",")]
     modes = args.profile_modes.split(",")
+    if modes[0].startswith("solve-"):  # a short block solve (cubes 192x128x96, m = 8) in the range
+        precond = modes[0][len("solve-"):]  # solve-amg | solve-chebyshev, host-driven loop
+        cop = gen.WORKLOADS["cubes192x128x96_m8"]["op"]()
+        A = ens.Matrix.from_operator(cop)
+        if precond == "amg":
+            A.amg_setup()
+        B = torch.from_numpy(gen.rhs_normal(cop.n, 8, 7, zero_mean=True)).cuda()
+        ens.solve_block(A, B, tol=1e-8, precond=precond)  # warm: workspace pools, code loaded
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        ens.solve_block(A, B, tol=1e-30, precond=precond, max_iter=args.steps, use_graph=0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        A.close()
+        print(json.dumps({"profile": "solve", "precond": precond, "workload": "cubes192x128x96", "m": 8, "iterations": args.steps}))
+        return 0
     if modes == ["projection"]:  # ens_divergence + ens_grad_correct, inside the NVTX range "profiled"
         import numpy as np
 
