@@ -242,7 +242,8 @@ ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_
  *              iteration on the level's matrix (smooth_steps updates, interval [cheb_lo, cheb_hi]
  *              of D^-1 A_l); the coarsest level runs coarse_steps Chebyshev updates.
  * The V-cycle is one fixed linear operator, applied to all m columns of a block at once (every
- * level's products are GSpMVs); ens_solve_block with ENS_PRECOND_AMG uses it as M^-1.
+ * level's products are GSpMVs); ens_solve_block with ENS_PRECOND_AMG uses it as M^-1. Each smoothed
+ * level also keeps the column-scaled copy A_l D_l^-1, so a two-update smoothing is one pass.
  */
 typedef struct {
   double theta;          /* strength threshold (default 0.08) */

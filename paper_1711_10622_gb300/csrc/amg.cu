@@ -140,6 +140,7 @@ void free_amg(ens_amg *H) {
   if (!H) return;
   for (ens_amg_lev &l : H->lev) {
     if (l.owned) ens_destroy_matrix(l.A);
+    ens_destroy_matrix(l.As);
     cudaFree(l.agg);
     cudaFree(l.agg_ptr);
     cudaFree(l.members);
@@ -196,6 +197,21 @@ extern "C" ens_status ens_amg_setup(ens_matrix *A, const ens_amg_opts *opts, voi
     HostCsr C = galerkin(L, agg, nc, ptr, mem);
     ens_amg_lev &f = H->lev.back();
     f.nc = nc;
+    // the column-scaled copy A D^-1 of this (smoothed) level: the first smoothing update needs
+    // A D^-1 src, one product of this copy instead of a scaled intermediate block
+    {
+      std::vector<double> dinv(L.n, 0.0), vs(L.val.size());
+      for (int64_t i = 0; i < L.n; ++i)
+        for (int32_t k = L.row[i]; k < L.row[i + 1]; ++k)
+          if (L.col[k] == i && L.val[k] != 0.0) dinv[i] = 1.0 / L.val[k];
+      for (int64_t i = 0; i < L.n; ++i)
+        for (int32_t k = L.row[i]; k < L.row[i + 1]; ++k) vs[k] = L.val[k] * dinv[L.col[k]];
+      st = ens_create_matrix(L.n, (int64_t)vs.size(), L.row.data(), L.col.data(), vs.data(), 0, stream, &f.As);
+      if (st != ENS_OK) {
+        free_amg(H);
+        return st;
+      }
+    }
     e = upload(&f.agg, agg, s);
     if (e == cudaSuccess) e = upload(&f.agg_ptr, ptr, s);
     if (e == cudaSuccess) e = upload(&f.members, mem, s);

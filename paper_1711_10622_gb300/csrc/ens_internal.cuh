@@ -52,6 +52,7 @@ struct ens_matrix {
 struct ens_amg_lev {
   ens_matrix *A = nullptr;
   bool owned = false;
+  ens_matrix *As = nullptr;     // A D^-1 (column-scaled copy, owned) on levels that are smoothed
   int64_t nc = 0;               // rows of the next level
   int32_t *agg = nullptr;       // [n] aggregate (next-level row) of each row
   int32_t *agg_ptr = nullptr;   // [nc + 1] start of each aggregate in members

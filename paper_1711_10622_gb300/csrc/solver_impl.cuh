@@ -669,6 +669,31 @@ __global__ void ENS_TILE_BOUNDS(Arith)
   });
 }
 
+// Both updates of a two-update Chebyshev smoothing in one pass, from the column-scaled copy
+// As = A D^-1 of the level (A d0 = As src / theta for d0 = D^-1 src / theta):
+//   d0 = D^-1 src / theta,  res1 = src - (As src) / theta,  d1 = c1 d0 + c2 D^-1 res1,
+//   z = d0 + d1  (ADD: z += d0 + d1).
+template <typename Arith, int VEC, int LANES, bool ADD>
+__global__ void ENS_TILE_BOUNDS(Arith)
+    k_amg_smooth2(MatView As, MatView A, int32_t m, const typename Arith::T *__restrict__ src, typename Arith::T *z,
+                  typename Arith::T inv_theta, typename Arith::T c1, typename Arith::T c2, uint32_t mask) {
+  using T = typename Arith::T;
+  tile_rows<Arith, VEC, LANES>(As, m, src, mask, [&](int64_t i, int32_t cc, const T (&w)[VEC]) {
+    T sv[VEC], zv[VEC];
+    load_vec<T, VEC>(src + i * m + cc, sv);
+    if (ADD) load_vec_rw<T, VEC>(z + i * m + cc, zv);
+    const T dv = Arith::dinv(A, i);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      const T d0 = dv * sv[q] * inv_theta;
+      const T r1 = sv[q] - w[q] * inv_theta;
+      const T d1 = c1 * d0 + c2 * (dv * r1);
+      zv[q] = ADD ? zv[q] + (d0 + d1) : d0 + d1;
+    }
+    store_vec<T, VEC>(z + i * m + cc, zv);
+  });
+}
+
 // rc_I = sum of res_i over the rows i of aggregate I (ascending rows: a fixed order).
 template <typename T, int VEC, int LANES>
 __global__ void __launch_bounds__(kThreads)
@@ -712,11 +737,13 @@ template <typename Arith>
 struct AmgCycle {
   using T = typename Arith::T;
   struct Level {
-    MatView A;
+    MatView A, As;
+    bool has_as = false;
     int64_t n = 0, nc = 0;
     const int32_t *agg = nullptr, *ptr = nullptr, *mem = nullptr;
-    uint32_t mask = 0;
-    bool split = false;  // float64 split arithmetic usable on this level
+    uint32_t mask = 0, as_mask = 0;
+    bool split = false;     // float64 split arithmetic usable on this level
+    bool as_split = false;  // ... and on its scaled copy
     int grid = 0, egrid = 0, cgrid = 0;
     T *r = nullptr, *z = nullptr, *res = nullptr, *cres = nullptr, *da = nullptr, *db = nullptr;
   };
@@ -742,6 +769,12 @@ struct AmgCycle {
       L.mem = h.members;
       L.split = use_split(h.A);
       L.mask = std::is_same<Arith, ArithF64Split>::value && L.split ? share_mask(native_share(h.A, mp)) : 0u;
+      if (h.As) {
+        L.has_as = true;
+        L.As = view_of(h.As);
+        L.as_split = use_split(h.As);
+        L.as_mask = std::is_same<Arith, ArithF64Split>::value && L.as_split ? share_mask(native_share(h.As, mp)) : 0u;
+      }
       const int64_t rows_per_block = kThreads / lanes;
       const int64_t sms = h.A->num_sms;
       L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + kTileRows - 1) / kTileRows, sms * TileBlocks<Arith>::value));
@@ -764,6 +797,24 @@ struct AmgCycle {
   template <typename Ar, int V, int Ln>
   void smooth(const Level &L, const T *src, T *z, bool add, int steps, cudaStream_t st) {
     const double theta = 0.5 * (o.cheb_hi + o.cheb_lo), delta = 0.5 * (o.cheb_hi - o.cheb_lo);
+    if (steps == 2 && L.has_as) {  // both updates in one pass over the scaled copy
+      const double sigma = theta / delta, rho_prev = 1.0 / sigma, rho = 1.0 / (2.0 * sigma - rho_prev);
+      const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta), it = (T)(1.0 / theta);
+      if constexpr (std::is_same<Ar, ArithF64Split>::value || std::is_same<Ar, ArithF64Hybrid>::value) {
+        if (!L.as_split) {  // the scaled copy's values leave the split range: native products
+          if (add)
+            k_amg_smooth2<ArithF64Native, V, Ln, true><<<L.grid, kThreads, 0, st>>>(L.As, L.A, mp, src, z, it, c1, c2, 0u);
+          else
+            k_amg_smooth2<ArithF64Native, V, Ln, false><<<L.grid, kThreads, 0, st>>>(L.As, L.A, mp, src, z, it, c1, c2, 0u);
+          return;
+        }
+      }
+      if (add)
+        k_amg_smooth2<Ar, V, Ln, true><<<L.grid, kThreads, 0, st>>>(L.As, L.A, mp, src, z, it, c1, c2, L.as_mask);
+      else
+        k_amg_smooth2<Ar, V, Ln, false><<<L.grid, kThreads, 0, st>>>(L.As, L.A, mp, src, z, it, c1, c2, L.as_mask);
+      return;
+    }
     if (add)
       k_amg_first<Ar, V, Ln, true><<<L.egrid, kThreads, 0, st>>>(L.A, mp, src, L.da, z, (T)(1.0 / theta));
     else

@@ -141,8 +141,9 @@ class Server:
                 levels = A.amg_setup() if precond == "amg" else [(op.n, op.nnz)]
                 # matrix copies held by the library per level (the fine one and, with AMG, the coarse
                 # ones): row_ptr, col, f64/f32/split values, inverse diagonals, aggregate maps
-                for n_l, nnz_l in levels:
-                    resident += 4 * (n_l + 1) + nnz_l * (4 + 8 + 4 + 8) + 12 * n_l + (8 * n_l if precond == "amg" else 0)
+                for k, (n_l, nnz_l) in enumerate(levels):
+                    copies = 2 if precond == "amg" and k < len(levels) - 1 else 1  # smoothed levels: + A D^-1
+                    resident += copies * (4 * (n_l + 1) + nnz_l * (4 + 8 + 4 + 8) + 12 * n_l) + (8 * n_l if precond == "amg" else 0)
         self.solve_fn = solve_fn or self._library_solve
         self.sched = Scheduler({k: op.n for k, op in operators.items()}, resident, budget_bytes, max_cols, precision)
         self.cv = threading.Condition()

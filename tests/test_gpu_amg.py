@@ -145,3 +145,24 @@ def test_amg_errors(ens):
         assert A.amg_info() == []
         A.amg_setup()
         assert len(A.amg_info()) >= 1
+
+
+@pytest.mark.parametrize("workload", ["cubes192x128x96_m8", "channel256x128x128"])
+def test_full_size_hierarchy_matches_oracle(ens, workload):
+    """The hierarchies of the full-size workloads: every level's aggregates and coarse operator
+    equal the oracle's (integer maps bit for bit, Galerkin sums in the same order), and one V-cycle
+    on sampled columns matches the oracle's on every row."""
+    op = gen.WORKLOADS[workload]["op"]()
+    H = oracle.AMG(op)
+    with ens.Matrix.from_operator(op) as A:
+        assert A.amg_setup() == H.sizes
+        for l in range(H.nlev):
+            row, col, val, agg = A.amg_level(l)
+            r2, c2, v2, a2 = H.level(l)
+            assert np.array_equal(row, r2) and np.array_equal(col, c2) and np.array_equal(val, v2)
+            if a2 is not None:
+                assert np.array_equal(agg, a2)
+        R = gen.rhs_normal(op.n, 2, 77, zero_mean=op.singular)
+        Z = ens.amg_apply(A, torch.from_numpy(R).cuda()).cpu().numpy()
+    ref = H.vcycle(R)
+    assert np.all(np.abs(Z - ref).max(axis=0) <= 1e-11 * np.abs(ref).max(axis=0))
