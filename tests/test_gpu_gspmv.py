@@ -60,7 +60,11 @@ OPS = {
     "dirichlet12": lambda: gen.dirichlet_box(12),
     "channel20x14x10": lambda: gen.channel(20, 14, 10),
     "cubes48x32x24": lambda: gen.cubes(48, 32, 24, size=4),
-    "random777": lambda: _random_csr(777, 3, long_rows=[(5, 70), (100, 65)]),
+    "random777": lambda: _random_csr(777, 3, long_rows=[(5, 70), (100, 65)]),  # rows > 64: native only
+    # split-eligible irregular rows: 0..12 nonzeros with empty rows, every tail-group size
+    "random_split": lambda: _random_csr(1000, 5, max_len=12, empty_frac=0.1),
+    # rows of up to 24 nonzeros: tile segments exceed the shared-memory tile (global-memory path)
+    "random_wide": lambda: _random_csr(600, 6, max_len=24, empty_frac=0.05),
     "one_row": lambda: _random_csr(1, 4, max_len=1, empty_frac=0.0),
 }
 _cache = {}
