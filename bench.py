@@ -212,9 +212,16 @@ def solve_metrics(reps: int = 2):
             return best, r
 
         res = {}
+        # reference solution for the error of every result: FP64 block solve to 1e-12
+        Xref, _ = ens.solve_block(A, B, tol=1e-12, precond="chebyshev" if pre == "chebyshev" else "none")
+
+        def rel_err(X):
+            return (torch.linalg.vector_norm(X - Xref, dim=0) / torch.linalg.vector_norm(Xref, dim=0)).max().item()
+
         for prec in ("f64", "mixed"):
             t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tol, precond=pre, precision=prec))
             res[prec] = {
+                "max_rel_err_vs_fp64_1e-12": rel_err(X),
                 "solves_per_s": m / t,
                 "seconds": t,
                 "max_relres": float(st["relres"].max()),
@@ -229,6 +236,7 @@ def solve_metrics(reps: int = 2):
             for prec in ("f64", "mixed"):
                 t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tol, precond="amg", precision=prec))
                 res[prec + "_amg"] = {
+                    "max_rel_err_vs_fp64_1e-12": rel_err(X),
                     "solves_per_s": m / t,
                     "seconds": t,
                     "max_relres": float(st["relres"].max()),
@@ -279,6 +287,49 @@ def cubes_gspmv_metrics(reps: int = 20):
     A.close()
     b = alg_bytes(op.n, op.nnz, m)
     return {"workload": "cubes192x128x96", "m": m, "n": op.n, "nnz": op.nnz, "us": us, "alg_mb": b / 1e6, "gbs": b / (us * 1e-6) / 1e9, "tuned": tuned}
+
+
+def batch_metrics(precond: str = "amg"):
+    """The batching workload: channel 256x192x192 (m = 16), 64^3 (m = 4), 128^3 (m = 8) and
+    96x160x96 (m = 32) in ONE ens_solve_batch launch, FP32 inner / FP64 refinement to 1e-10.
+    RHS-solves/s of the batch (set-up of the preconditioner excluded), per-system iterations and
+    the solution error of each system against its FP64 block solve to 1e-12."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_1711_10622_gb300 as ens
+
+    specs = [((256, 192, 192), 16), ((64, 64, 64), 4), ((128, 128, 128), 8), ((96, 160, 96), 32)]
+    mats, Bs = [], []
+    try:
+        for i, (dims, m) in enumerate(specs):
+            op = gen.channel(*dims)
+            A = ens.Matrix.from_operator(op)
+            if precond == "amg":
+                A.amg_setup()
+            mats.append(A)
+            Bs.append(torch.from_numpy(gen.rhs_normal(op.n, m, 10622 + 40 + i, zero_mean=True)).cuda())
+        items = [(A, B, None, 1e-10) for A, B in zip(mats, Bs)]
+        ens.solve_batch(items, precond=precond, precision="mixed")  # warm: graph code paths, pools
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ens.solve_batch(items, precond=precond, precision="mixed")
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        systems = []
+        for (dims, m), A, B, (X, st) in zip(specs, mats, Bs, res):
+            Xr, _ = ens.solve_block(A, B, tol=1e-12, precond=precond)
+            err = (torch.linalg.vector_norm(X - Xr, dim=0) / torch.linalg.vector_norm(Xr, dim=0)).max().item()
+            systems.append({"grid": "x".join(map(str, dims)), "m": m, "converged": int((st["status"] == 0).sum()),
+                            "max_relres": float(np.max(st["relres"])), "iters_max": int(np.max(st["iters"])),
+                            "outer_max": int(np.max(st["outer"])), "max_rel_err_vs_fp64": err})
+    finally:
+        for A in mats:
+            A.close()
+    rhs = sum(m for _, m in specs)
+    return {"precond": precond, "precision": "mixed", "tol": 1e-10, "rhs": rhs, "seconds": t, "rhs_solves_per_s": rhs / t,
+            "systems": systems}
 
 
 def fp64_peak_ops(sm_mhz=None):
@@ -741,6 +792,7 @@ def main():
     solves = None if args.no_solves else solve_metrics()
     projection = None if args.no_solves else projection_metrics()
     cubes = None if args.no_solves else cubes_gspmv_metrics()
+    batch = None if args.no_solves else batch_metrics()
     if cubes is not None:
         cubes["frac_of_measured_peak"] = cubes["gbs"] / peak
     if projection is not None:
@@ -786,6 +838,7 @@ def main():
             "solves": solves,
             "projection": projection,
             "cubes_gspmv": cubes,
+            "batch": batch,
             "serving": serving,
             "paper_estimate": estimate,
             "cpu_baseline": cpu,
