@@ -26,6 +26,8 @@ struct ens_grid {
   uint8_t *open = nullptr;         // [n] bit 2d: low face along d open, bit 2d+1: high face open
   double *width[3] = {nullptr, nullptr, nullptr};     // [N_d] cell widths
   double *inv_dist[3] = {nullptr, nullptr, nullptr};  // [N_d + 1] per face position (see below)
+  double *area[3] = {nullptr, nullptr, nullptr};      // face areas normal to d, indexed by the other two
+                                                      // coordinates (lower one fastest)
 };
 
 namespace ens {
@@ -43,6 +45,7 @@ struct GridView {
   const uint8_t *__restrict__ open;
   const double *__restrict__ width[3];
   const double *__restrict__ inv_dist[3];
+  const double *__restrict__ area[3];
 };
 
 GridView view_of(const ens_grid *G) {
@@ -52,6 +55,7 @@ GridView view_of(const ens_grid *G) {
     v.F[d] = G->F[d];
     v.bc[d] = G->bc[d];
     v.width[d] = G->width[d];
+    v.area[d] = G->area[d];
     v.inv_dist[d] = G->inv_dist[d];
   }
   v.n = G->n;
@@ -111,14 +115,15 @@ __global__ void __launch_bounds__(kThreads)
     const int32_t cell = g.all_fluid ? r : g.cell_of_row[r];
     const int32_t p[3] = {cell % g.N[0], (cell / g.N[0]) % g.N[1], cell / (g.N[0] * g.N[1])};
     const uint32_t op = g.open[r];
-    const double w[3] = {g.width[0][p[0]], g.width[1][p[1]], g.width[2][p[2]]};
+    // face areas of the cell (tables of the products of the other two widths)
+    const double ar[3] = {g.area[0][p[1] + (int64_t)g.N[1] * p[2]], g.area[1][p[0] + (int64_t)g.N[0] * p[2]],
+                          g.area[2][p[0] + (int64_t)g.N[0] * p[1]]};
     double acc[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      // area of the cell's faces normal to d: product of the widths in the other directions
-      const double area = d == 0 ? w[1] * w[2] : (d == 1 ? w[0] * w[2] : w[0] * w[1]);
+      const double area = ar[d];
       int32_t lo[3] = {p[0], p[1], p[2]}, hi[3] = {p[0], p[1], p[2]};
       hi[d] = (g.bc[d] == ENS_BC_PERIODIC && p[d] + 1 == g.N[d]) ? 0 : p[d] + 1;
       if (op & (2u << (2 * d))) {
@@ -215,6 +220,7 @@ void free_grid(ens_grid *G) {
   for (int d = 0; d < 3; ++d) {
     cudaFree(G->width[d]);
     cudaFree(G->inv_dist[d]);
+    cudaFree(G->area[d]);
   }
   delete G;
 }
@@ -312,6 +318,16 @@ extern "C" ens_status ens_create_grid(int32_t nx, int32_t ny, int32_t nz, const 
     }
   }
 
+  // area of the faces normal to d: the product of the cell widths in the other two directions
+  // (ascending direction order), tabulated over those two coordinates
+  std::vector<double> area[3];
+  for (int d = 0; d < 3; ++d) {
+    const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;  // the other two directions, a < b
+    area[d].resize((size_t)N[a] * N[b]);
+    for (int32_t jb = 0; jb < N[b]; ++jb)
+      for (int32_t ja = 0; ja < N[a]; ++ja) area[d][ja + (size_t)N[a] * jb] = width[a][ja] * width[b][jb];
+  }
+
   ens_grid *G = new ens_grid();
   for (int d = 0; d < 3; ++d) {
     G->N[d] = N[d];
@@ -335,6 +351,7 @@ extern "C" ens_status ens_create_grid(int32_t nx, int32_t ny, int32_t nz, const 
   for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
     e = upload(&G->width[d], width[d], s);
     if (e == cudaSuccess) e = upload(&G->inv_dist[d], inv_dist[d], s);
+    if (e == cudaSuccess) e = upload(&G->area[d], area[d], s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
