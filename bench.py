@@ -261,32 +261,36 @@ def solve_metrics(reps: int = 2):
 
 
 def cubes_gspmv_metrics(reps: int = 20):
-    """FP64 GSpMV on the wall-mounted-cube operator 192 x 128 x 96 (rows of 5-7 nonzeros) at m = 8,
-    autotuned: device time per launch (CUDA events, 3 warm-up launches) and algorithmic GB/s."""
+    """FP64 GSpMV on the wall-mounted-cube operator 192 x 128 x 96 (rows of 5-7 nonzeros) for
+    m = 1..32, each width autotuned: device time per launch (CUDA events around `reps` launches
+    after 3 warm-up launches, inputs resident) and algorithmic GB/s."""
     import torch
 
     import gen
     import paper_1711_10622_gb300 as ens
 
     op = gen.WORKLOADS["cubes192x128x96_m8"]["op"]()
-    m = 8
     A = ens.Matrix.from_operator(op)
-    tuned = A.autotune(m, "f64")
-    X = torch.from_numpy(gen.rhs_normal(op.n, m, 20100)).cuda()
-    Y = torch.empty_like(X)
-    for _ in range(3):
-        ens.gspmv(A, X, Y)
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    s.record()
-    for _ in range(reps):
-        ens.gspmv(A, X, Y)
-    e.record()
-    torch.cuda.synchronize()
-    us = s.elapsed_time(e) / reps * 1e3
+    sweep = {}
+    for m in M_SWEEP:
+        tuned = A.autotune(m, "f64")
+        X = torch.from_numpy(gen.rhs_normal(op.n, m, 20100 + m)).cuda()
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            ens.gspmv(A, X, Y)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(reps):
+            ens.gspmv(A, X, Y)
+        e.record()
+        torch.cuda.synchronize()
+        us = s.elapsed_time(e) / reps * 1e3
+        b = alg_bytes(op.n, op.nnz, m)
+        sweep[str(m)] = {"us": us, "alg_mb": b / 1e6, "gbs": b / (us * 1e-6) / 1e9, "tuned": tuned}
+        del X, Y
     A.close()
-    b = alg_bytes(op.n, op.nnz, m)
-    return {"workload": "cubes192x128x96", "m": m, "n": op.n, "nnz": op.nnz, "us": us, "alg_mb": b / 1e6, "gbs": b / (us * 1e-6) / 1e9, "tuned": tuned}
+    return {"workload": "cubes192x128x96", "n": op.n, "nnz": op.nnz, "sweep": sweep}
 
 
 def batch_metrics(precond: str = "amg"):
@@ -375,8 +379,10 @@ def projection_metrics(m: int = 8, reps: int = 20):
     G.close()
     b_div = 8 * m * (faces + op.n) + op.n  # faces read, D written, open-face mask
     b_cor = 8 * m * (2 * faces + op.n) + op.n  # faces read and written, P read, mask
-    ops_div = 7 * op.n * m  # 6 DFMA + 1 DMUL per cell and state
-    ops_cor = 9 * op.n * m  # per owned face: difference, scaling, update
+    ops_div = 7 * op.n * m  # 6 DFMA + 1 DMUL per cell and state (face areas are tabulated)
+    # per owned face and state a difference and an update, plus one tau * inv_dist product per face
+    # shared by the 4 states a thread carries (m = 8)
+    ops_cor = int((6 + 3 / 4) * op.n * m)
     return {
         "workload": "channel256x128x128",
         "m": m,
@@ -794,7 +800,8 @@ def main():
     cubes = None if args.no_solves else cubes_gspmv_metrics()
     batch = None if args.no_solves else batch_metrics()
     if cubes is not None:
-        cubes["frac_of_measured_peak"] = cubes["gbs"] / peak
+        for v in cubes["sweep"].values():
+            v["frac_of_measured_peak"] = v["gbs"] / peak
     if projection is not None:
         ceiling = fp64_peak_ops(clocks.get("sm_mhz") if isinstance(clocks, dict) else None) / 1e9
         for k in ("divergence", "grad_correct"):

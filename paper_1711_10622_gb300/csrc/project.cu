@@ -1,7 +1,8 @@
 // The projection step around the pressure solve for m flow states (Section 2.2, Eqs. eq2/eq3):
 // the divergence of m staggered velocity fields (the Poisson right-hand sides) and the pressure-
 // gradient correction u -= tau G p. Both are streaming passes over the fluid cells with the m
-// states of a face contiguous in memory (row-interleaved), one thread per (cell, column pair).
+// states of a face contiguous in memory (row-interleaved), one thread per (cell, group of 1, 2 or 4
+// states).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,32 +67,41 @@ GridView view_of(const ens_grid *G) {
   return v;
 }
 
+// VEC consecutive doubles (VEC = 1, 2 or 4; 16-byte aligned for 2 and 4).
 template <int VEC>
 __device__ __forceinline__ void ldv(const double *p, double (&v)[VEC]) {
-  if constexpr (VEC == 2) {
-    const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
-    v[0] = t.x;
-    v[1] = t.y;
-  } else {
+  if constexpr (VEC == 1) {
     v[0] = __ldg(p);
+  } else {
+#pragma unroll
+    for (int h = 0; h < VEC / 2; ++h) {
+      const double2 t = __ldg(reinterpret_cast<const double2 *>(p) + h);
+      v[2 * h] = t.x;
+      v[2 * h + 1] = t.y;
+    }
   }
 }
 template <int VEC>
 __device__ __forceinline__ void ldv_rw(const double *p, double (&v)[VEC]) {
-  if constexpr (VEC == 2) {
-    const double2 t = *reinterpret_cast<const double2 *>(p);
-    v[0] = t.x;
-    v[1] = t.y;
-  } else {
+  if constexpr (VEC == 1) {
     v[0] = *p;
+  } else {
+#pragma unroll
+    for (int h = 0; h < VEC / 2; ++h) {
+      const double2 t = reinterpret_cast<const double2 *>(p)[h];
+      v[2 * h] = t.x;
+      v[2 * h + 1] = t.y;
+    }
   }
 }
 template <int VEC>
 __device__ __forceinline__ void stv(double *p, const double (&v)[VEC]) {
-  if constexpr (VEC == 2)
-    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
-  else
+  if constexpr (VEC == 1) {
     *p = v[0];
+  } else {
+#pragma unroll
+    for (int h = 0; h < VEC / 2; ++h) reinterpret_cast<double2 *>(p)[h] = make_double2(v[2 * h], v[2 * h + 1]);
+  }
 }
 
 // Face array index of the face at position (c0, c1, c2) along d (c_d is the face number).
@@ -403,11 +413,16 @@ extern "C" ens_status ens_divergence(const ens_grid *G, int32_t m, double scale,
   for (int d = 0; d < 3; ++d)
     if (overlaps(D, nd, comp[d], (size_t)G->nfaces[d] * m * sizeof(double)))
       return fail(ENS_ERR_INVALID, "divergence: D overlaps a velocity component");
-  const bool vec2 = m % 2 == 0 && aligned16(U) && aligned16(V) && aligned16(W) && aligned16(D);
+  // four or two states per thread when the rows allow 16-byte accesses: the per-cell work (coordinates,
+  // open faces, areas) is shared by those states
+  const bool al = aligned16(U) && aligned16(V) && aligned16(W) && aligned16(D);
+  const int vec = al && m % 4 == 0 ? 4 : (al && m % 2 == 0 ? 2 : 1);
   const GridView g = view_of(G);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t work = (int64_t)G->n * (vec2 ? m / 2 : m);
-  if (vec2)
+  const int64_t work = (int64_t)G->n * (m / vec);
+  if (vec == 4)
+    k_divergence<4><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
+  else if (vec == 2)
     k_divergence<2><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
   else
     k_divergence<1><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
@@ -431,11 +446,14 @@ extern "C" ens_status ens_grad_correct(const ens_grid *G, int32_t m, double tau,
       if (overlaps(comp[d], nb, comp[e], (size_t)G->nfaces[e] * m * sizeof(double)))
         return fail(ENS_ERR_INVALID, "grad_correct: velocity components overlap");
   }
-  const bool vec2 = m % 2 == 0 && aligned16(P) && aligned16(U) && aligned16(V) && aligned16(W);
+  const bool al = aligned16(P) && aligned16(U) && aligned16(V) && aligned16(W);
+  const int vec = al && m % 4 == 0 ? 4 : (al && m % 2 == 0 ? 2 : 1);
   const GridView g = view_of(G);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t work = (int64_t)G->n * (vec2 ? m / 2 : m);
-  if (vec2)
+  const int64_t work = (int64_t)G->n * (m / vec);
+  if (vec == 4)
+    k_grad_correct<4><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, tau, P, U, V, W);
+  else if (vec == 2)
     k_grad_correct<2><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, tau, P, U, V, W);
   else
     k_grad_correct<1><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, tau, P, U, V, W);
