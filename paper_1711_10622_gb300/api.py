@@ -100,7 +100,10 @@ class Matrix:
         ens_amg_opts: theta, max_levels, coarse_size, smooth_steps, coarse_steps, cheb_lo, cheb_hi."""
         o = N.AmgOpts()
         N.lib().ens_default_amg_opts(ctypes.byref(o))
+        known = {f[0] for f in N.AmgOpts._fields_}
         for k, v in opts.items():
+            if k not in known:
+                raise TypeError(f"unknown AMG option {k!r}; expected one of {sorted(known)}")
             setattr(o, k, v)
         N.check(N.lib().ens_amg_setup(self.handle, ctypes.byref(o), _stream_handle(stream)))
         return self.amg_info()
@@ -212,7 +215,10 @@ def solve_opts(**kw) -> N.SolveOpts:
     given by name: 'none' | 'chebyshev' | 'amg', 'f64' | 'mixed')."""
     o = N.SolveOpts()
     N.lib().ens_default_solve_opts(ctypes.byref(o))
+    known = {f[0] for f in N.SolveOpts._fields_}
     for k, v in kw.items():
+        if k not in known:
+            raise TypeError(f"unknown solve option {k!r}; expected one of {sorted(known)}")
         if v is None:
             continue
         if k == "precond":

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <new>
 #include <vector>
 
 #include "ens_internal.cuh"
@@ -163,8 +164,18 @@ extern "C" void ens_default_amg_opts(ens_amg_opts *o) {
   o->cheb_hi = 2.0;
 }
 
+static ens_status amg_setup_impl(ens_matrix *A, const ens_amg_opts *opts, void *stream);
+
 extern "C" ens_status ens_amg_setup(ens_matrix *A, const ens_amg_opts *opts, void *stream) {
   clear_error();
+  try {
+    return amg_setup_impl(A, opts, stream);
+  } catch (const std::bad_alloc &) {
+    return fail(ENS_ERR_OOM, "amg_setup: host allocation failed");
+  }
+}
+
+static ens_status amg_setup_impl(ens_matrix *A, const ens_amg_opts *opts, void *stream) {
   if (!A) return fail(ENS_ERR_INVALID, "amg_setup: matrix is NULL");
   ens_amg_opts o;
   ens_default_amg_opts(&o);

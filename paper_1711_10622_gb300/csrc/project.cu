@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <new>
 #include <vector>
 
 #include "ens_internal.cuh"
@@ -247,10 +248,24 @@ cudaError_t upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
 
 using namespace ens;
 
+static ens_status create_grid_impl(int32_t nx, int32_t ny, int32_t nz, const double *xn, const double *yn,
+                                   const double *zn, const int32_t *bc, const uint8_t *solid, void *stream,
+                                   ens_grid **out);
+
 extern "C" ens_status ens_create_grid(int32_t nx, int32_t ny, int32_t nz, const double *xn, const double *yn,
                                       const double *zn, const int32_t *bc, const uint8_t *solid, void *stream,
                                       ens_grid **out) {
   clear_error();
+  try {
+    return create_grid_impl(nx, ny, nz, xn, yn, zn, bc, solid, stream, out);
+  } catch (const std::bad_alloc &) {
+    return fail(ENS_ERR_OOM, "create_grid: host allocation failed");
+  }
+}
+
+static ens_status create_grid_impl(int32_t nx, int32_t ny, int32_t nz, const double *xn, const double *yn,
+                                   const double *zn, const int32_t *bc, const uint8_t *solid, void *stream,
+                                   ens_grid **out) {
   if (!out) return fail(ENS_ERR_INVALID, "create_grid: out is NULL");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1) return fail(ENS_ERR_INVALID, "create_grid: dimensions must be >= 1");
