@@ -102,7 +102,7 @@ ens_status ens_set_native_share(ens_matrix *A, int32_t share);
 /*
  * Autotuner: time the GSpMV launch candidates for block width m (1..64) and dtype on this matrix
  * (lanes per row, i.e. rows per warp and column-tile width; for FP64 also native DFMA vs split-float
- * with native shares 0, 8, 16, 24 of 32, and the column hybrid) and keep the fastest for later
+ * with native shares 0, 8, 12, 16, 24 of 32, and the column hybrid) and keep the fastest for later
  * ens_gspmv calls and for the solver's products of that width. Uses temporary device blocks of
  * n x m (stream-ordered, freed before return). Synchronous. Optional outputs: chosen lanes, chosen
  * share (32 = native, 64 = column hybrid), and the best time per launch in microseconds. A share

@@ -55,8 +55,11 @@ __global__ void __launch_bounds__(kThreads)
 #ifndef ENS_SPLIT_MIN_BLOCKS
 #define ENS_SPLIT_MIN_BLOCKS 6
 #endif
+#ifndef ENS_SPLIT4_MIN_BLOCKS
+#define ENS_SPLIT4_MIN_BLOCKS 5  // four columns per lane: 48 registers
+#endif
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads, ENS_SPLIT_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, VEC == 4 ? ENS_SPLIT4_MIN_BLOCKS : ENS_SPLIT_MIN_BLOCKS)
     gspmv_kernel_capped(MatView A, int32_t m, const typename Arith::T *__restrict__ X,
                         typename Arith::T *__restrict__ Y, uint32_t native_mask) {
   gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
@@ -120,11 +123,10 @@ int native_share(const ens_matrix *A, int m) {
   if (A->f64_mode == ENS_F64_SPLIT) return 0;
   if (m >= 1 && m <= kTuneMaxM && A->tuned_share[m] >= 0) return A->tuned_share[m];
   // Measured on GB300 (channel 256 x 128 x 128): native DFMA is fastest up to m = 2; beyond, about
-  // 12/32 of the row sweeps on the FP64 pipe (16/32 from m = 32) and the rest split is fastest
-  // (m = 32: 1148 us against 1461 us all split and 1723 us all native).
+  // 12/32 of the row sweeps on the FP64 pipe and the rest split is fastest (m = 32: 928 us against
+  // 1091 us all split and 1709 us all native).
   if (m <= 2) return 32;
-  if (m < 32) return 12;
-  return 16;
+  return 12;
 }
 
 // Bit s set for about share/32 of the sweep indices s = 0..31, spread evenly.
@@ -143,6 +145,23 @@ struct Cfg {
   int vec, lanes, share;
 };
 
+// VEC and full-width lanes of a float64 launch with native share `share`: split-float products take
+// four columns per lane when m allows (two packed float pairs share each nonzero's index and
+// matrix pair; measured on GB300, channel 256 x 128 x 128, m = 8..32: 9-11 % faster than two),
+// native DFMA and the column hybrid two.
+void f64_shape(int m, int share, bool al16, int &vec, int &lanes) {
+  if (share < 32 && m % 4 == 0 && al16) {
+    vec = 4;
+    lanes = pow2_at_least(m / 4, 8);
+  } else if (m % 2 == 0 && al16) {
+    vec = 2;
+    lanes = pow2_at_least(m / 2, 16);
+  } else {
+    vec = 1;
+    lanes = pow2_at_least(m, 32);
+  }
+}
+
 Cfg default_cfg(const ens_matrix *A, int m, int dtype, const void *X, const void *Y) {
   Cfg c{};
   if (dtype == ENS_F32) {
@@ -158,14 +177,12 @@ Cfg default_cfg(const ens_matrix *A, int m, int dtype, const void *X, const void
     }
     c.share = 0;
   } else {
-    const bool vec2 = (m % 2 == 0) && aligned(X, 16) && aligned(Y, 16);
-    c.vec = vec2 ? 2 : 1;
-    c.lanes = vec2 ? pow2_at_least(m / 2, 16) : pow2_at_least(m, 32);
     c.share = use_split(A) ? native_share(A, m) : 32;
+    f64_shape(m, c.share, aligned(X, 16) && aligned(Y, 16), c.vec, c.lanes);
   }
   if (m >= 1 && m <= kTuneMaxM) {
     const int tl = A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m];
-    if (tl > 0 && tl <= c.lanes) c.lanes = tl;  // tuned for the same VEC (alignment permitting)
+    if (tl > 0 && tl <= c.lanes) c.lanes = tl;  // tuned for the same share, hence VEC (alignment permitting)
   }
   return c;
 }
@@ -182,6 +199,7 @@ cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, voi
   }
   if (c.share < 32) {
     const uint32_t mask = share_mask(c.share);
+    if (c.vec == 4) return dispatch<ArithF64Split, 4>(A, m, X, Y, c.lanes, mask, s);
     return c.vec == 2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, c.lanes, mask, s)
                       : dispatch<ArithF64Split, 1>(A, m, X, Y, c.lanes, mask, s);
   }
@@ -213,9 +231,10 @@ ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, vo
   return ENS_OK;
 }
 
-// Autotuner: time every candidate (lanes per row: full, half and quarter column tile; FP64
-// arithmetic: native DFMA and split with native shares 0, 8, 16, 24) on this matrix for block width
-// m with CUDA events, keep the fastest in the matrix's table.
+// Autotuner: time every candidate (FP64 arithmetic: native DFMA, split with native shares 0, 8, 12,
+// 16, 24 and the column hybrid; for each, lanes per row giving the full, half and quarter column
+// tile of its VEC) on this matrix for block width m with CUDA events, keep the fastest in the
+// matrix's table.
 ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *lanes_out, int32_t *share_out,
                     double *best_us_out) {
   const size_t count = (size_t)A->n * m;
@@ -235,17 +254,19 @@ ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *la
   if (dtype != ENS_F32) A->tuned_share[m] = -1;
   const Cfg base = default_cfg(A, m, dtype, X, Y);
   std::vector<Cfg> cand;
-  for (int div = 1; div <= 4; div *= 2) {
-    const int lanes = base.lanes / div;
-    if (lanes < 1) break;
-    if (dtype == ENS_F32) {
-      cand.push_back(Cfg{base.vec, lanes, 0});
-    } else {
-      cand.push_back(Cfg{base.vec, lanes, 32});
-      if (use_split(A)) {
-        for (int sh : {0, 8, 16, 24}) cand.push_back(Cfg{base.vec, lanes, sh});
-        if (base.vec == 2) cand.push_back(Cfg{base.vec, lanes, kShareHybrid});
-      }
+  auto add_widths = [&](int vec, int full, int share) {
+    for (int div = 1; div <= 4 && full / div >= 1; div *= 2) cand.push_back(Cfg{vec, full / div, share});
+  };
+  if (dtype == ENS_F32) {
+    add_widths(base.vec, base.lanes, 0);
+  } else {
+    std::vector<int> shares{32};
+    if (use_split(A)) shares.insert(shares.end(), {0, 8, 12, 16, 24, kShareHybrid});
+    for (int sh : shares) {
+      int vec = 1, full = 1;
+      f64_shape(m, sh, true, vec, full);  // the tuning blocks are 256-byte aligned
+      if (sh == kShareHybrid && vec != 2) continue;
+      add_widths(vec, full, sh);
     }
   }
   cudaEvent_t t0 = nullptr, t1 = nullptr;

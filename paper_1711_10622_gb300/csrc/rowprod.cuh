@@ -34,7 +34,43 @@ struct Vec<float, 2> { using type = float2; };
 template <>
 struct Vec<float, 4> { using type = float4; };
 
-// VEC consecutive elements starting at p (p aligned to VEC * sizeof(T)).
+// VEC consecutive elements starting at p (p aligned to VEC * sizeof(T); 16 bytes for 4 doubles,
+// which move as two 16-byte halves).
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(const T *__restrict__ p, T (&v)[VEC]);
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec_rw(const T *p, T (&v)[VEC]);
+template <typename T, int VEC>
+__device__ __forceinline__ void store_vec(T *p, const T (&v)[VEC]);
+template <typename T, int VEC>
+__device__ __forceinline__ void store_vec_cs(T *p, const T (&v)[VEC]);
+template <>
+__device__ __forceinline__ void load_vec<double, 4>(const double *__restrict__ p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void load_vec_rw<double, 4>(const double *p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void store_vec<double, 4>(double *p, const double (&v)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store_vec_cs<double, 4>(double *p, const double (&v)[4]) {
+  __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+  __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
+}
+
 template <typename T, int VEC>
 __device__ __forceinline__ void load_vec(const T *__restrict__ p, T (&v)[VEC]) {
   using V = typename Vec<T, VEC>::type;
@@ -409,6 +445,62 @@ __device__ __forceinline__ void row_split2(int32_t j0, int32_t j1, const int32_t
   }
 }
 
+// Four columns per lane: the two packed pairs of row_split2 share each nonzero's index and matrix
+// pairs; gathers of kUnroll / 2 nonzeros (two 16-byte halves each) are issued together.
+template <typename AV>
+__device__ __forceinline__ void row_split4(int32_t j0, int32_t j1, const int32_t *ci, const AV *va,
+                                           const double *__restrict__ vn, int32_t m, int32_t c,
+                                           const double *__restrict__ X, double (&y)[4]) {
+  constexpr int G = kUnroll / 2;
+  static_assert(G == 2, "the tail below handles one left-over nonzero");
+  uint64_t sh0 = 0ull, sl0 = 0ull, sh1 = 0ull, sl1 = 0ull;
+  uint32_t rng[4] = {0u, 0u, 0u, 0u};
+  const uint64_t g23 = f2_pack(__uint_as_float(kSplitG), __uint_as_float(kSplitG));
+  const char *xc = reinterpret_cast<const char *>(X + c);
+  const uint32_t rb = (uint32_t)m * 8u;
+  int32_t j = j0;
+  for (; j + G <= j1; j += G) {
+    double2 x[G][2];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const double2 *px = xrow(xc, ci[j + u], rb);
+      x[u][0] = __ldg(px);
+      x[u][1] = __ldg(px + 1);
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const SplitPair a = split_pair(va[j + u]);
+      split_acc2(a, x[u][0].x, x[u][0].y, g23, sh0, sl0, rng[0], rng[1]);
+      split_acc2(a, x[u][1].x, x[u][1].y, g23, sh1, sl1, rng[2], rng[3]);
+    }
+  }
+  if (j < j1) {  // one left-over nonzero (G = 2)
+    const double2 *px = xrow(xc, ci[j], rb);
+    const double2 x0 = __ldg(px), x1 = __ldg(px + 1);
+    const SplitPair a = split_pair(va[j]);
+    split_acc2(a, x0.x, x0.y, g23, sh0, sl0, rng[0], rng[1]);
+    split_acc2(a, x1.x, x1.y, g23, sh1, sl1, rng[2], rng[3]);
+  }
+  float h[4], l[4];
+  f2_unpack(sh0, h[0], h[1]);
+  f2_unpack(sh1, h[2], h[3]);
+  f2_unpack(sl0, l[0], l[1]);
+  f2_unpack(sl1, l[2], l[3]);
+  bool ok[4], all_ok = true;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ok[q] = split_ok(rng[q], h[q], l[q]);
+    y[q] = split_to_double(h[q], l[q]);
+    all_ok &= ok[q];
+  }
+  if (!all_ok) {
+    double z[4];
+    row_native_f64<4>(j0, j1, ci, vn, m, c, X, z);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) y[q] = ok[q] ? y[q] : z[q];
+  }
+}
+
 // ------------------------------------------------------------------ row tiles (shared memory)
 constexpr int kTileRows = 256;
 constexpr int kTileNnz = 2048;
@@ -542,6 +634,8 @@ struct ArithF64Split {
       row_native_f64<VEC>(j0, j1, sm.ci, A.val + ab, m, c, X, y);
     } else if constexpr (VEC == 2) {
       row_split2<float2>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
+    } else if constexpr (VEC == 4) {
+      row_split4<float2>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
     } else {
       row_split<VEC>(j0, j1, sm.ci, A.vs + ab, A.val + ab, m, c, X, y);
     }
@@ -553,6 +647,8 @@ struct ArithF64Split {
       row_native_f64<VEC>(j0, j1, A.ci + ab, A.val + ab, m, c, X, y);
     } else if constexpr (VEC == 2) {
       row_split2<float2>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
+    } else if constexpr (VEC == 4) {
+      row_split4<float2>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
     } else {
       row_split<VEC>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
     }

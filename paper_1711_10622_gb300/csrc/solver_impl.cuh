@@ -88,7 +88,6 @@ __global__ void ENS_TILE_BOUNDS(Arith)
             typename Arith::T incompat, Cols<typename Arith::T> cs, typename Arith::T *partials,
             unsigned *counter, uint32_t mask) {
   using T = typename Arith::T;
-  const int32_t c = (threadIdx.x % LANES) * VEC;
   T acc[3][VEC];
 #pragma unroll
   for (int d = 0; d < 3; ++d)

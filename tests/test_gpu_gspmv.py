@@ -100,7 +100,7 @@ M_VALUES = [1, 2, 3, 4, 5, 7, 8, 16, 32, 33, 64]
 
 @pytest.mark.parametrize("name", list(OPS))
 @pytest.mark.parametrize("m", M_VALUES)
-@pytest.mark.parametrize("mode", ["auto", "native", "hybrid", "f32"])
+@pytest.mark.parametrize("mode", ["auto", "native", "split", "hybrid", "f32"])
 def test_gspmv_parity(ens, name, m, mode):
     op = _op(name)
     X = gen.rhs_normal(op.n, m, 1000 + m)
@@ -230,7 +230,7 @@ def test_full_size_channel_sampled(ens, m):
         assert np.all(np.abs(Y32 - ref) <= 1e-5 * scale)
 
 
-@pytest.mark.parametrize("share", [0, 8, 16, 24, 32])
+@pytest.mark.parametrize("share", [0, 8, 12, 16, 24, 32])
 def test_hybrid_native_share_parity(ens, share):
     """Every split/native mix of the FP64 product stays within the FP64 bound."""
     op = _op("cubes48x32x24")
@@ -249,7 +249,7 @@ def test_autotune_then_parity(ens):
             for dt in ("f64", "f32"):
                 r = A.autotune(m, dt)
                 assert r["lanes"] >= 1 and r["best_us"] > 0
-                assert r["share"] in (0, 8, 16, 24, 32, 64) or dt == "f32"  # 64: column hybrid
+                assert r["share"] in (0, 8, 12, 16, 24, 32, 64) or dt == "f32"  # 64: column hybrid
                 X = gen.rhs_normal(op.n, m, 500 + m)
                 if dt == "f64":
                     Y = ens.gspmv(A, torch.from_numpy(X).cuda()).cpu().numpy()
