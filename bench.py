@@ -180,9 +180,10 @@ def cpu_baseline_sweep(op, seconds_cap: float = 30.0):
 
 
 def solve_metrics(reps: int = 2):
-    """RHS-solves/s of the block solver against the one-RHS-at-a-time FP64 solver (the same
-    library, m = 1, looped over the columns) on the configured solve workloads. Each solve is
-    timed end to end around the synchronous ens_solve_block call (inputs resident on the GPU)."""
+    """RHS-solves/s of the block solver against the one-RHS-at-a-time solver (the same library,
+    m = 1, looped over the columns) on the configured solve workloads: against FP64 with the plain
+    preconditioner, and like for like (same preconditioner and precision). Each solve is timed end to
+    end around the synchronous ens_solve_block call (inputs resident on the GPU)."""
     import torch
 
     import gen
@@ -246,10 +247,15 @@ def solve_metrics(reps: int = 2):
                 }
             res["amg_setup_s"] = t_setup
             res["amg_levels"] = levels
+        # one-RHS-at-a-time baselines: the same solver with m = 1 looped over the columns, for every
+        # preconditioner and precision above (like for like), and FP64 with the plain preconditioner
         cols = [B[:, l : l + 1].contiguous() for l in range(m)]
-        t1, outs = timed(lambda: [ens.solve_block(A, c, tol=tol, precond=pre, precision="f64") for c in cols])
-        base = m / t1
-        res["one_rhs_f64"] = {"solves_per_s": base, "seconds": t1, "iters": [int(o[1]["iters"][0]) for o in outs]}
+        for key in [k for k in ("f64", "mixed", "f64_amg", "mixed_amg") if k in res]:
+            prec, _, p1 = key.partition("_")
+            t1, outs = timed(lambda: [ens.solve_block(A, c, tol=tol, precond=p1 or pre, precision=prec) for c in cols])
+            res["one_rhs_" + key] = {"solves_per_s": m / t1, "seconds": t1, "iters": [int(o[1]["iters"][0]) for o in outs]}
+            res[key]["speedup_vs_one_rhs_same"] = res[key]["solves_per_s"] / res["one_rhs_" + key]["solves_per_s"]
+        base = res["one_rhs_f64"]["solves_per_s"]
         for prec in ("f64", "mixed", "f64_amg", "mixed_amg"):
             if prec in res:
                 res[prec]["speedup_vs_one_rhs_f64"] = res[prec]["solves_per_s"] / base
@@ -393,11 +399,13 @@ def projection_metrics(m: int = 8, reps: int = 20):
     }
 
 
-def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float = 120e9, slots: int = 4):
-    """Poisson stream of solve requests (grids 64^3..192^3, channel and cube operators, m drawn from
-    {1, 2, 4, 8, 16, 32}, FP32 inner + FP64 refinement to 1e-8, AMG-lite preconditioner) through the continuous-
-    batching server under an HBM budget. The arrival rate is `load` times the capacity measured by a
-    saturated burst of the same requests. Latency = arrival to result on the host."""
+def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = 5, budget: float = 120e9, slots: int = 4):
+    """Poisson streams of solve requests (grids 64^3..192^3, channel and cube operators, m drawn from
+    {1, 2, 4, 8, 16, 32}, FP32 inner + FP64 refinement to 1e-8, AMG-lite preconditioner) through the
+    continuous-batching server under an HBM budget. The arrival rate of each stream is `load` times
+    the capacity measured by a saturated burst of the same requests (one stream per load, the same
+    requests and arrival seed). Latency = arrival to result on the host. The first load's summary is
+    the top level; every load's summary is under "loads"."""
     import gen
     from paper_1711_10622_gb300.serving import Request, Server, latency_summary
 
@@ -411,6 +419,7 @@ def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float 
         c0 = int(rng.integers(0, 64 - m + 1))
         return Request(name, pools[name][:, c0 : c0 + m].copy(), 1e-8)
 
+    out = []
     with Server(ops, budget_bytes=budget, slots=slots, max_cols=32, precond="amg") as srv:
         burst_n = min(16, count)
         burst = [srv.submit(make(n, m)) for n, m, _ in reqs[:burst_n]]
@@ -418,38 +427,43 @@ def serving_metrics(count: int, load: float = 0.7, seed: int = 5, budget: float 
             r.done.wait(600)
         span = max(r.end for r in burst) - min(r.arrival for r in burst)
         cap_rps = burst_n / span
-        rate = load * cap_rps
-        arrivals = gen.poisson_arrivals(count, rate, seed)
-        pending = [make(n, m) for n, m, _ in reqs]
-        t0 = time.perf_counter()
-        for r, ta in zip(pending, arrivals):
-            dt = t0 + ta - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            srv.submit(r)
-        for r in pending:
-            r.done.wait(900)
-        peak = srv.sched.peak_in_flight + srv.sched.resident
-        unfinished = sum(1 for r in pending if not r.done.is_set())
-        pending = [r for r in pending if r.done.is_set()]
-    s = latency_summary(pending)
-    s.update(
-        {
-            "arrival_rate_per_s": rate,
-            "load_vs_measured_capacity": load,
-            "capacity_requests_per_s": cap_rps,
-            "budget_gb": budget / 1e9,
-            "peak_admitted_gb": peak / 1e9,
-            "slots": slots,
-            "grids": sorted(ops),
-            "tol": 1e-8,
-            "precision": "mixed",
-            "precond": "amg",
-            "converged_all": all((r.stats is not None and (r.stats["status"] == 0).all()) for r in pending),
-            "unfinished": unfinished,
-        }
-    )
-    return s
+        for load in loads:
+            rate = load * cap_rps
+            arrivals = gen.poisson_arrivals(count, rate, seed)
+            pending = [make(n, m) for n, m, _ in reqs]
+            srv.sched.peak_in_flight = 0
+            t0 = time.perf_counter()
+            for r, ta in zip(pending, arrivals):
+                dt = t0 + ta - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                srv.submit(r)
+            for r in pending:
+                r.done.wait(900)
+            peak = srv.sched.peak_in_flight + srv.sched.resident
+            unfinished = sum(1 for r in pending if not r.done.is_set())
+            pending = [r for r in pending if r.done.is_set()]
+            s = latency_summary(pending)
+            s.update(
+                {
+                    "arrival_rate_per_s": rate,
+                    "load_vs_measured_capacity": load,
+                    "capacity_requests_per_s": cap_rps,
+                    "budget_gb": budget / 1e9,
+                    "peak_admitted_gb": peak / 1e9,
+                    "slots": slots,
+                    "grids": sorted(ops),
+                    "tol": 1e-8,
+                    "precision": "mixed",
+                    "precond": "amg",
+                    "converged_all": all((r.stats is not None and (r.stats["status"] == 0).all()) for r in pending),
+                    "unfinished": unfinished,
+                }
+            )
+            out.append(s)
+    top = dict(out[0])
+    top["loads"] = {str(s["load_vs_measured_capacity"]): {k: s[k] for k in ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "rhs_solves_per_s", "arrival_rate_per_s", "peak_admitted_gb", "errors", "converged_all", "unfinished") if k in s} for s in out}
+    return top
 
 
 def run_reference(args):

@@ -48,18 +48,22 @@ __global__ void __launch_bounds__(kThreads)
   gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
 }
 
-// The split path with a register cap (at least 6 resident blocks per SM, 40 registers): the
-// gather-latency-bound loop needs resident warps more than registers (measured on GB300: 6 blocks
-// beat 5 by 1-10 % over m = 2..32; with a minimum of one block per SM the compiler took 125-140
-// registers and every launch ran at half speed).
-#ifndef ENS_SPLIT_MIN_BLOCKS
-#define ENS_SPLIT_MIN_BLOCKS 6
-#endif
-#ifndef ENS_SPLIT4_MIN_BLOCKS
-#define ENS_SPLIT4_MIN_BLOCKS 5  // four columns per lane: 48 registers
-#endif
+// Register caps (minimum resident blocks per SM) for the gather-latency-bound kernels, which need
+// resident warps more than registers. Measured on GB300, channel 256 x 128 x 128:
+//   * split float64, two columns per lane: 6 blocks, 40 registers (6 beat 5 by 1-10 % over
+//     m = 2..32; 7 or 8 blocks spill and lose 1-10 %);
+//   * split float64, four columns per lane: 5 blocks, 48 registers (6 spill 164-212 bytes; 4 blocks
+//     with 64 registers lose 2-12 %);
+//   * float32: 8 blocks, 32 registers (10-12 % faster than the compiler's own 40 registers over
+//     m = 8..32).
+// Native float64 keeps the compiler's choice: any minimum-blocks bound, even one block, let the
+// compiler take 125-140 registers there and halved every launch.
+template <typename Arith, int VEC>
+struct MinBlocks {
+  static constexpr int value = std::is_same<Arith, ArithF32>::value ? 8 : VEC == 4 ? 5 : 6;
+};
 template <typename Arith, int VEC, int LANES>
-__global__ void __launch_bounds__(kThreads, VEC == 4 ? ENS_SPLIT4_MIN_BLOCKS : ENS_SPLIT_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, MinBlocks<Arith, VEC>::value)
     gspmv_kernel_capped(MatView A, int32_t m, const typename Arith::T *__restrict__ X,
                         typename Arith::T *__restrict__ Y, uint32_t native_mask) {
   gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
@@ -77,7 +81,7 @@ int grid_for(const ens_matrix *A, const void *kernel) {
 template <typename Arith, int VEC, int LANES>
 cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, cudaStream_t s) {
   using T = typename Arith::T;
-  if constexpr (std::is_same<Arith, ArithF64Split>::value) {
+  if constexpr (std::is_same<Arith, ArithF64Split>::value || std::is_same<Arith, ArithF32>::value) {
     auto k = gspmv_kernel_capped<Arith, VEC, LANES>;
     k<<<grid_for(A, (const void *)k), kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
   } else {

@@ -34,81 +34,75 @@ struct Vec<float, 2> { using type = float2; };
 template <>
 struct Vec<float, 4> { using type = float4; };
 
-// VEC consecutive elements starting at p (p aligned to VEC * sizeof(T); 16 bytes for 4 doubles,
-// which move as two 16-byte halves).
+// One access of a VEC-element vector: a single load or store of VEC elements, except for float64
+// vectors wider than two, which move as VEC / 2 16-byte halves.
 template <typename T, int VEC>
-__device__ __forceinline__ void load_vec(const T *__restrict__ p, T (&v)[VEC]);
-template <typename T, int VEC>
-__device__ __forceinline__ void load_vec_rw(const T *p, T (&v)[VEC]);
-template <typename T, int VEC>
-__device__ __forceinline__ void store_vec(T *p, const T (&v)[VEC]);
-template <typename T, int VEC>
-__device__ __forceinline__ void store_vec_cs(T *p, const T (&v)[VEC]);
-template <>
-__device__ __forceinline__ void load_vec<double, 4>(const double *__restrict__ p, double (&v)[4]) {
-  const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-  v[0] = a.x;
-  v[1] = a.y;
-  v[2] = b.x;
-  v[3] = b.y;
-}
-template <>
-__device__ __forceinline__ void load_vec_rw<double, 4>(const double *p, double (&v)[4]) {
-  const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-  v[0] = a.x;
-  v[1] = a.y;
-  v[2] = b.x;
-  v[3] = b.y;
-}
-template <>
-__device__ __forceinline__ void store_vec<double, 4>(double *p, const double (&v)[4]) {
-  reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-  reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void store_vec_cs<double, 4>(double *p, const double (&v)[4]) {
-  __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
-  __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
-}
+struct Access {
+  using type = typename Vec<T, VEC>::type;
+  static constexpr int n = VEC;
+};
+template <int VEC>
+struct Access<double, VEC> {
+  using type = typename Vec<double, (VEC > 1 ? 2 : 1)>::type;
+  static constexpr int n = VEC > 1 ? 2 : 1;
+};
 
+// VEC consecutive elements starting at p (p aligned to the access width: VEC * sizeof(T), 16 bytes
+// for float64 vectors of two or more).
 template <typename T, int VEC>
 __device__ __forceinline__ void load_vec(const T *__restrict__ p, T (&v)[VEC]) {
-  using V = typename Vec<T, VEC>::type;
-  const V t = __ldg(reinterpret_cast<const V *>(p));
-  const T *e = reinterpret_cast<const T *>(&t);
+  using A = Access<T, VEC>;
+  using V = typename A::type;
 #pragma unroll
-  for (int q = 0; q < VEC; ++q) v[q] = e[q];
+  for (int h = 0; h < VEC / A::n; ++h) {
+    const V t = __ldg(reinterpret_cast<const V *>(p) + h);
+    const T *e = reinterpret_cast<const T *>(&t);
+#pragma unroll
+    for (int q = 0; q < A::n; ++q) v[h * A::n + q] = e[q];
+  }
 }
 
 // Same, for data written earlier in the same kernel launch by this thread (no read-only path).
 template <typename T, int VEC>
 __device__ __forceinline__ void load_vec_rw(const T *p, T (&v)[VEC]) {
-  using V = typename Vec<T, VEC>::type;
-  const V t = *reinterpret_cast<const V *>(p);
-  const T *e = reinterpret_cast<const T *>(&t);
+  using A = Access<T, VEC>;
+  using V = typename A::type;
 #pragma unroll
-  for (int q = 0; q < VEC; ++q) v[q] = e[q];
+  for (int h = 0; h < VEC / A::n; ++h) {
+    const V t = reinterpret_cast<const V *>(p)[h];
+    const T *e = reinterpret_cast<const T *>(&t);
+#pragma unroll
+    for (int q = 0; q < A::n; ++q) v[h * A::n + q] = e[q];
+  }
 }
 
 template <typename T, int VEC>
 __device__ __forceinline__ void store_vec(T *p, const T (&v)[VEC]) {
-  using V = typename Vec<T, VEC>::type;
-  V t;
-  T *e = reinterpret_cast<T *>(&t);
+  using A = Access<T, VEC>;
+  using V = typename A::type;
 #pragma unroll
-  for (int q = 0; q < VEC; ++q) e[q] = v[q];
-  *reinterpret_cast<V *>(p) = t;
+  for (int h = 0; h < VEC / A::n; ++h) {
+    V t;
+    T *e = reinterpret_cast<T *>(&t);
+#pragma unroll
+    for (int q = 0; q < A::n; ++q) e[q] = v[h * A::n + q];
+    reinterpret_cast<V *>(p)[h] = t;
+  }
 }
 
 // Streaming store (evict-first): for outputs written once and not re-read soon.
 template <typename T, int VEC>
 __device__ __forceinline__ void store_vec_cs(T *p, const T (&v)[VEC]) {
-  using V = typename Vec<T, VEC>::type;
-  V t;
-  T *e = reinterpret_cast<T *>(&t);
+  using A = Access<T, VEC>;
+  using V = typename A::type;
 #pragma unroll
-  for (int q = 0; q < VEC; ++q) e[q] = v[q];
-  __stcs(reinterpret_cast<V *>(p), t);
+  for (int h = 0; h < VEC / A::n; ++h) {
+    V t;
+    T *e = reinterpret_cast<T *>(&t);
+#pragma unroll
+    for (int q = 0; q < A::n; ++q) e[q] = v[h * A::n + q];
+    __stcs(reinterpret_cast<V *>(p) + h, t);
+  }
 }
 
 constexpr int kUnroll = 4;
@@ -124,39 +118,40 @@ template <typename T, typename V, int VEC>
 __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t *ci, const V *va, int32_t m,
                                           int32_t c, const T *__restrict__ X, T (&acc)[VEC]) {
   constexpr bool kGroupTail = sizeof(T) == 4;
+  constexpr int U = kUnroll;
 #pragma unroll
   for (int q = 0; q < VEC; ++q) acc[q] = T(0);
   int32_t j = j0;
-  for (; j + kUnroll <= j1; j += kUnroll) {
-    int32_t k[kUnroll];
-    T a[kUnroll];
+  for (; j + U <= j1; j += U) {
+    int32_t k[U];
+    T a[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       k[u] = ci[j + u];
       a[u] = (T)va[j + u];
     }
-    T x[kUnroll][VEC];
+    T x[U][VEC];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
+    for (int u = 0; u < U; ++u) load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int q = 0; q < VEC; ++q) acc[q] = fma(a[u], x[u][q], acc[q]);
   }
   if (kGroupTail) {
     if (j < j1) {
       const int32_t len = j1 - j;
-      int32_t k[kUnroll];
-      T a[kUnroll];
-      T x[kUnroll][VEC];
+      int32_t k[U];
+      T a[U];
+      T x[U][VEC];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < U; ++u) {
         const bool v = u < len;
         k[u] = v ? ci[j + u] : 0;
         a[u] = v ? (T)va[j + u] : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < U; ++u) {
         if (u < len) {
           load_vec<T, VEC>(X + (int64_t)k[u] * m + c, x[u]);
         } else {
@@ -165,7 +160,7 @@ __device__ __forceinline__ void row_plain(int32_t j0, int32_t j1, const int32_t 
         }
       }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int q = 0; q < VEC; ++q)
           if (u < len) acc[q] = fma(a[u], x[u][q], acc[q]);
@@ -445,59 +440,73 @@ __device__ __forceinline__ void row_split2(int32_t j0, int32_t j1, const int32_t
   }
 }
 
-// Four columns per lane: the two packed pairs of row_split2 share each nonzero's index and matrix
-// pairs; gathers of kUnroll / 2 nonzeros (two 16-byte halves each) are issued together.
-template <typename AV>
-__device__ __forceinline__ void row_split4(int32_t j0, int32_t j1, const int32_t *ci, const AV *va,
-                                           const double *__restrict__ vn, int32_t m, int32_t c,
-                                           const double *__restrict__ X, double (&y)[4]) {
-  constexpr int G = kUnroll / 2;
-  static_assert(G == 2, "the tail below handles one left-over nonzero");
-  uint64_t sh0 = 0ull, sl0 = 0ull, sh1 = 0ull, sl1 = 0ull;
-  uint32_t rng[4] = {0u, 0u, 0u, 0u};
+// Four or more columns per lane: NP packed pairs of row_split2 share each nonzero's column index
+// and matrix pair; gathers of kUnroll / NP nonzeros (NP 16-byte pieces each) are issued together.
+// The kernels use NP = 2 (eight columns per lane, NP = 4, needs 64-80 registers, spills, and was
+// 15-20 % slower on GB300).
+template <int NP, typename AV>
+__device__ __forceinline__ void row_split_pairs(int32_t j0, int32_t j1, const int32_t *ci, const AV *va,
+                                                const double *__restrict__ vn, int32_t m, int32_t c,
+                                                const double *__restrict__ X, double (&y)[2 * NP]) {
+  constexpr int G = kUnroll / NP > 1 ? kUnroll / NP : 1;
+  uint64_t sh[NP], sl[NP];
+  uint32_t rng[2 * NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    sh[p] = sl[p] = 0ull;
+    rng[2 * p] = rng[2 * p + 1] = 0u;
+  }
   const uint64_t g23 = f2_pack(__uint_as_float(kSplitG), __uint_as_float(kSplitG));
   const char *xc = reinterpret_cast<const char *>(X + c);
   const uint32_t rb = (uint32_t)m * 8u;
   int32_t j = j0;
   for (; j + G <= j1; j += G) {
-    double2 x[G][2];
+    double2 x[G][NP];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const double2 *px = xrow(xc, ci[j + u], rb);
-      x[u][0] = __ldg(px);
-      x[u][1] = __ldg(px + 1);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) x[u][p] = __ldg(px + p);
     }
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const SplitPair a = split_pair(va[j + u]);
-      split_acc2(a, x[u][0].x, x[u][0].y, g23, sh0, sl0, rng[0], rng[1]);
-      split_acc2(a, x[u][1].x, x[u][1].y, g23, sh1, sl1, rng[2], rng[3]);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) split_acc2(a, x[u][p].x, x[u][p].y, g23, sh[p], sl[p], rng[2 * p], rng[2 * p + 1]);
     }
   }
-  if (j < j1) {  // one left-over nonzero (G = 2)
-    const double2 *px = xrow(xc, ci[j], rb);
-    const double2 x0 = __ldg(px), x1 = __ldg(px + 1);
-    const SplitPair a = split_pair(va[j]);
-    split_acc2(a, x0.x, x0.y, g23, sh0, sl0, rng[0], rng[1]);
-    split_acc2(a, x1.x, x1.y, g23, sh1, sl1, rng[2], rng[3]);
-  }
-  float h[4], l[4];
-  f2_unpack(sh0, h[0], h[1]);
-  f2_unpack(sh1, h[2], h[3]);
-  f2_unpack(sl0, l[0], l[1]);
-  f2_unpack(sl1, l[2], l[3]);
-  bool ok[4], all_ok = true;
+  auto one = [&](int32_t jj) {
+    const double2 *px = xrow(xc, ci[jj], rb);
+    double2 x[NP];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+    for (int p = 0; p < NP; ++p) x[p] = __ldg(px + p);
+    const SplitPair a = split_pair(va[jj]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) split_acc2(a, x[p].x, x[p].y, g23, sh[p], sl[p], rng[2 * p], rng[2 * p + 1]);
+  };
+  if constexpr (G == 2) {  // the last 1..G-1 nonzeros
+    if (j < j1) one(j);
+  } else if constexpr (G > 2) {
+    for (; j < j1; ++j) one(j);
+  }
+  float h[2 * NP], l[2 * NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    f2_unpack(sh[p], h[2 * p], h[2 * p + 1]);
+    f2_unpack(sl[p], l[2 * p], l[2 * p + 1]);
+  }
+  bool ok[2 * NP], all_ok = true;
+#pragma unroll
+  for (int q = 0; q < 2 * NP; ++q) {
     ok[q] = split_ok(rng[q], h[q], l[q]);
     y[q] = split_to_double(h[q], l[q]);
     all_ok &= ok[q];
   }
   if (!all_ok) {
-    double z[4];
-    row_native_f64<4>(j0, j1, ci, vn, m, c, X, z);
+    double z[2 * NP];
+    row_native_f64<2 * NP>(j0, j1, ci, vn, m, c, X, z);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) y[q] = ok[q] ? y[q] : z[q];
+    for (int q = 0; q < 2 * NP; ++q) y[q] = ok[q] ? y[q] : z[q];
   }
 }
 
@@ -635,7 +644,7 @@ struct ArithF64Split {
     } else if constexpr (VEC == 2) {
       row_split2<float2>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
     } else if constexpr (VEC == 4) {
-      row_split4<float2>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
+      row_split_pairs<2, float2>(j0, j1, sm.ci, sm.va, A.val + ab, m, c, X, y);
     } else {
       row_split<VEC>(j0, j1, sm.ci, A.vs + ab, A.val + ab, m, c, X, y);
     }
@@ -648,7 +657,7 @@ struct ArithF64Split {
     } else if constexpr (VEC == 2) {
       row_split2<float2>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
     } else if constexpr (VEC == 4) {
-      row_split4<float2>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
+      row_split_pairs<2, float2>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
     } else {
       row_split<VEC>(j0, j1, A.ci + ab, A.vs + ab, A.val + ab, m, c, X, y);
     }

@@ -78,6 +78,15 @@ struct TileBlocks<ArithF64Hybrid> {
   static constexpr int value = 5;
 };
 #define ENS_TILE_BOUNDS(Arith) __launch_bounds__(kThreads, TileBlocks<Arith>::value)
+// GSpMV kernels without column reductions (k_cheb, k_amg_resid, k_amg_smooth2) hold fewer live
+// registers: their float32 forms run at 8 blocks and 32 registers, like the standalone float32
+// GSpMV (10-12 % faster there than at 6 blocks); with the reductions' accumulators the float32
+// k_start / k_v / k_t / k_resid would spill 56-300 bytes at 32 registers and stay at 6.
+template <typename Arith>
+struct LightBlocks {
+  static constexpr int value = std::is_same<Arith, ArithF32>::value ? 8 : TileBlocks<Arith>::value;
+};
+#define ENS_LIGHT_BOUNDS(Arith) __launch_bounds__(kThreads, LightBlocks<Arith>::value)
 
 // ----------------------------------------------------------------------------- start
 // r = b - A x (or r = b and x = 0 when x0_zero), rhat = r; per column ||b||^2, ||r||^2, sum(b).
@@ -201,7 +210,7 @@ __global__ void __launch_bounds__(kThreads)
 // din is the GSpMV input (read by neighbouring rows), so d_k goes to a second buffer. The last
 // step needs neither res_k nor d_k afterwards.
 template <typename Arith, int VEC, int LANES, bool FIRST, bool LAST>
-__global__ void ENS_TILE_BOUNDS(Arith)
+__global__ void ENS_LIGHT_BOUNDS(Arith)
     k_cheb(MatView A, int32_t m, const typename Arith::T *__restrict__ din, typename Arith::T *__restrict__ dout,
            const typename Arith::T *__restrict__ src, typename Arith::T *res, typename Arith::T *z,
            typename Arith::T c1, typename Arith::T c2, uint32_t mask) {
@@ -655,7 +664,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // res = r - A z
 template <typename Arith, int VEC, int LANES>
-__global__ void ENS_TILE_BOUNDS(Arith)
+__global__ void ENS_LIGHT_BOUNDS(Arith)
     k_amg_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ z, const typename Arith::T *__restrict__ r,
                 typename Arith::T *__restrict__ res, uint32_t mask) {
   using T = typename Arith::T;
@@ -673,7 +682,7 @@ __global__ void ENS_TILE_BOUNDS(Arith)
 //   d0 = D^-1 src / theta,  res1 = src - (As src) / theta,  d1 = c1 d0 + c2 D^-1 res1,
 //   z = d0 + d1  (ADD: z += d0 + d1).
 template <typename Arith, int VEC, int LANES, bool ADD>
-__global__ void ENS_TILE_BOUNDS(Arith)
+__global__ void ENS_LIGHT_BOUNDS(Arith)
     k_amg_smooth2(MatView As, MatView A, int32_t m, const typename Arith::T *__restrict__ src, typename Arith::T *z,
                   typename Arith::T inv_theta, typename Arith::T c1, typename Arith::T c2, uint32_t mask) {
   using T = typename Arith::T;
@@ -776,7 +785,7 @@ struct AmgCycle {
       }
       const int64_t rows_per_block = kThreads / lanes;
       const int64_t sms = h.A->num_sms;
-      L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + kTileRows - 1) / kTileRows, sms * TileBlocks<Arith>::value));
+      L.grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + kTileRows - 1) / kTileRows, sms * LightBlocks<Arith>::value));
       L.egrid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + rows_per_block - 1) / rows_per_block, sms * 8));
       L.cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((L.nc + rows_per_block - 1) / rows_per_block, sms * 8));
       const size_t blk = (size_t)L.n * mp;
@@ -882,7 +891,7 @@ struct Bicg {
   using T = typename Arith::T;
   MatView A;
   int64_t n = 0;
-  int mp = 0, vec = 2, lanes = 1, grid = 0, tgrid = 0;  // grid: streaming kernels, tgrid: GSpMV kernels
+  int mp = 0, vec = 2, lanes = 1, grid = 0, tgrid = 0, lgrid = 0;  // grid: streaming kernels, tgrid / lgrid: GSpMV kernels
   bool prec = false;
   bool use_amg = false;
   AmgCycle<Arith> amg;
@@ -908,6 +917,7 @@ struct Bicg {
     while (lanes * vec < mp) lanes <<= 1;
     grid = M->num_sms * 4;
     tgrid = M->num_sms * TileBlocks<Arith>::value;
+    lgrid = M->num_sms * LightBlocks<Arith>::value;
     prec = o.precond == ENS_PRECOND_CHEBYSHEV;
     cheb_steps = o.cheb_steps;
     theta = 0.5 * (o.cheb_hi + o.cheb_lo);
@@ -982,13 +992,13 @@ struct Bicg {
       const T c1 = (T)(rho * rho_prev), c2 = (T)(2.0 * rho / delta);
       const bool first = k == 1, last = k == cheb_steps - 1;
       if (first && last)
-        k_cheb<Arith, V, L, true, true><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, true, true><<<lgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (first)
-        k_cheb<Arith, V, L, true, false><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, true, false><<<lgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else if (last)
-        k_cheb<Arith, V, L, false, true><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, false, true><<<lgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       else
-        k_cheb<Arith, V, L, false, false><<<tgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
+        k_cheb<Arith, V, L, false, false><<<lgrid, kThreads, 0, st>>>(A, mp, din, dout, src, res, z, c1, c2, mask);
       std::swap(din, dout);
       rho_prev = rho;
     }
