@@ -126,10 +126,12 @@ int native_share(const ens_matrix *A, int m) {
   if (A->native_share >= 0) return A->native_share;
   if (A->f64_mode == ENS_F64_SPLIT) return 0;
   if (m >= 1 && m <= kTuneMaxM && A->tuned_share[m] >= 0) return A->tuned_share[m];
-  // Measured on GB300 (channel 256 x 128 x 128): native DFMA is fastest up to m = 2; beyond, about
-  // 12/32 of the row sweeps on the FP64 pipe and the rest split is fastest (m = 32: 928 us against
-  // 1091 us all split and 1709 us all native).
+  // Measured on GB300 (channel 256 x 128 x 128): native DFMA is fastest up to m = 2; at m = 4 nearly
+  // all split (4/32: 180 us, against 195 us with 12/32); from m = 8 about 12/32 of the row sweeps
+  // on the FP64 pipe and the rest split (m = 32: 928 us against 1077 us all split and 1695 us all
+  // native).
   if (m <= 2) return 32;
+  if (m < 8) return 4;
   return 12;
 }
 

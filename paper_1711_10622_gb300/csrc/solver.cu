@@ -7,6 +7,7 @@
 #include <string>
 
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "ens_internal.cuh"
@@ -199,7 +200,10 @@ template <typename Arith>
 ens_status amg_apply_impl(const ens_matrix *A, int32_t m, const void *R, void *Z, cudaStream_t s) {
   using T = typename Arith::T;
   const int32_t mp = m == 1 ? 1 : (m + 1) & ~1;
-  const int vec = mp == 1 ? 1 : 2;
+  // the solver's column mapping: four float32 columns per lane where the width and (for unpadded
+  // blocks, which are used in place) the 16-byte alignment allow, two otherwise
+  const bool al16 = mp != m || ((uintptr_t)R % 16 == 0 && (uintptr_t)Z % 16 == 0);
+  const int vec = mp == 1 ? 1 : (std::is_same<Arith, ArithF32>::value && mp % 4 == 0 && al16) ? 4 : 2;
   int lanes = 1;
   while (lanes * vec < mp) lanes <<= 1;
   const int64_t n = A->n;

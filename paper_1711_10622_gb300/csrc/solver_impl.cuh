@@ -580,10 +580,22 @@ static __global__ void k_unpad(int64_t n, int32_t m, int32_t mp, const double *_
 }
 
 // ----------------------------------------------------------------------------- host side
-template <typename F>
+// VEC (1, 2, or 4 where kVec4) and LANES (a power of two) as compile-time constants.
+template <bool kVec4 = false, typename F>
 cudaError_t with_vl(int vec, int lanes, F &&f) {
   using std::integral_constant;
   if (vec == 1) return f(integral_constant<int, 1>{}, integral_constant<int, 1>{});
+  if constexpr (kVec4) {
+    if (vec == 4) {
+      switch (lanes) {
+        case 1: return f(integral_constant<int, 4>{}, integral_constant<int, 1>{});
+        case 2: return f(integral_constant<int, 4>{}, integral_constant<int, 2>{});
+        case 4: return f(integral_constant<int, 4>{}, integral_constant<int, 4>{});
+        case 8: return f(integral_constant<int, 4>{}, integral_constant<int, 8>{});
+        default: return f(integral_constant<int, 4>{}, integral_constant<int, 16>{});
+      }
+    }
+  }
   switch (lanes) {
     case 1: return f(integral_constant<int, 2>{}, integral_constant<int, 1>{});
     case 2: return f(integral_constant<int, 2>{}, integral_constant<int, 2>{});
@@ -743,6 +755,7 @@ __global__ void __launch_bounds__(kThreads)
 
 template <typename Arith>
 struct AmgCycle {
+  static constexpr bool kVec4 = std::is_same<Arith, ArithF32>::value;  // float32 blocks: 4 columns per lane
   using T = typename Arith::T;
   struct Level {
     MatView A, As;
@@ -878,7 +891,7 @@ struct AmgCycle {
 
   // z = V(r) on the fine level (capturable: kernel launches only).
   cudaError_t apply(const T *r, T *z, cudaStream_t st) {
-    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+    return with_vl<kVec4>(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, Ln = decltype(Lc)::value;
       this->template cycle<V, Ln>(0, r, z, st);
       return cudaGetLastError();
@@ -888,6 +901,9 @@ struct AmgCycle {
 
 template <typename Arith>
 struct Bicg {
+  // float32 blocks whose padded width is a multiple of 4 take four columns per lane (16-byte
+  // accesses, as the standalone float32 GSpMV); float64 blocks two.
+  static constexpr bool kVec4 = std::is_same<Arith, ArithF32>::value;
   using T = typename Arith::T;
   MatView A;
   int64_t n = 0;
@@ -912,7 +928,7 @@ struct Bicg {
     mp = mp_;
     mask = std::is_same<Arith, ArithF64Split>::value ? share_mask(native_share(M, mp_)) : 0u;
     s = st;
-    vec = mp == 1 ? 1 : 2;
+    vec = mp == 1 ? 1 : (kVec4 && mp % 4 == 0) ? 4 : 2;
     lanes = 1;
     while (lanes * vec < mp) lanes <<= 1;
     grid = M->num_sms * 4;
@@ -967,7 +983,7 @@ struct Bicg {
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, (size_t)n * mp * sizeof(T), st);
     if (e != cudaSuccess) return e;
     const T incompat = (T)(1e-10 * std::sqrt((double)n));
-    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+    return with_vl<kVec4>(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       k_start<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, b, x, r, rh, x0_zero ? 1 : 0, singular, incompat, cs,
                                                       partials, counter, mask);
@@ -1008,7 +1024,7 @@ struct Bicg {
   // lives on the device, so the same launches can be captured once and replayed.
   cudaError_t iteration(T *x, int max_iter, cudaStream_t st) {
     const T inv_theta = (T)(1.0 / theta);
-    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+    return with_vl<kVec4>(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       if (prec) {
         k_p<Arith, V, L, true><<<grid, kThreads, 0, st>>>(A, mp, r, p, v, da, ph, inv_theta, cs);
@@ -1124,7 +1140,7 @@ struct Bicg {
 
   cudaError_t finish(const T *b, T *x, int singular, cudaStream_t st = nullptr) {
     if (!st) st = s;
-    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+    return with_vl<kVec4>(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       if (singular) {
         k_colsum<Arith, V, L><<<grid, kThreads, 0, st>>>(A, mp, x, (T)(1.0 / (double)n), cs, partials, counter);
@@ -1137,7 +1153,7 @@ struct Bicg {
 
   cudaError_t outer_residual(const T *b, const T *x, cudaStream_t st = nullptr) {
     if (!st) st = s;
-    return with_vl(vec, lanes, [&](auto Vc, auto Lc) {
+    return with_vl<kVec4>(vec, lanes, [&](auto Vc, auto Lc) {
       constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
       k_resid<Arith, V, L><<<tgrid, kThreads, 0, st>>>(A, mp, b, x, r, 1, cs, partials, counter, mask);
       return cudaGetLastError();
