@@ -521,7 +521,9 @@ def run_profile(args):
     """Launch-only mode for ncu captures: W + K GSpMV launches per (m, arithmetic) on a channel
     operator of the requested size, no timing output; with --profile-modes projection, W + K
     divergence + correction pairs on that channel's grid instead; with solve-amg / solve-chebyshev,
-    K BiCGStab iterations of the cube workload (192 x 128 x 96, m = 8, host-driven loop) instead.
+    K BiCGStab iterations of the cube workload (192 x 128 x 96, m = 8, host-driven loop) instead
+    (solve-amg-mixed / solve-chebyshev-mixed: one outer step of the mixed solve, K FP32 inner
+    iterations).
     Sizes: 'full' = 256 x 128 x 128,
     'half' = 128 x 128 x 128 (inputs still larger than L2, a few GB on the device at most)."""
     import torch
@@ -537,20 +539,27 @@ def run_profile(args):
     ms = [int(v) for v in args.profile_m.split(",")]
     modes = args.profile_modes.split(",")
     if modes[0].startswith("solve-"):  # a short block solve (cubes 192x128x96, m = 8) in the range
-        precond = modes[0][len("solve-"):]  # solve-amg | solve-chebyshev, host-driven loop
+        # solve-amg | solve-chebyshev (FP64), or with "-mixed": one outer step of the mixed-precision
+        # solve whose FP32 inner solve runs K iterations; host-driven loop
+        precond, _, mixed = modes[0][len("solve-"):].partition("-")
         cop = gen.WORKLOADS["cubes192x128x96_m8"]["op"]()
         A = ens.Matrix.from_operator(cop)
         if precond == "amg":
             A.amg_setup()
         B = torch.from_numpy(gen.rhs_normal(cop.n, 8, 7, zero_mean=True)).cuda()
-        ens.solve_block(A, B, tol=1e-8, precond=precond)  # warm: workspace pools, code loaded
+        prec = "mixed" if mixed == "mixed" else "f64"
+        ens.solve_block(A, B, tol=1e-8, precond=precond, precision=prec)  # warm: workspace pools, code loaded
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("profiled")
-        ens.solve_block(A, B, tol=1e-30, precond=precond, max_iter=args.steps, use_graph=0)
+        if prec == "mixed":
+            ens.solve_block(A, B, tol=1e-30, precond=precond, precision="mixed", max_outer=1, inner_tol=1e-30,
+                            inner_max_iter=args.steps, use_graph=0)
+        else:
+            ens.solve_block(A, B, tol=1e-30, precond=precond, max_iter=args.steps, use_graph=0)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         A.close()
-        print(json.dumps({"profile": "solve", "precond": precond, "workload": "cubes192x128x96", "m": 8, "iterations": args.steps}))
+        print(json.dumps({"profile": "solve", "precond": precond, "precision": prec, "workload": "cubes192x128x96", "m": 8, "iterations": args.steps}))
         return 0
     if modes == ["projection"]:  # ens_divergence + ens_grad_correct, inside the NVTX range "profiled"
         import numpy as np
