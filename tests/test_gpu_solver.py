@@ -108,6 +108,27 @@ def test_mixed_precision_matches_fp64_oracle(ens, precond):
         assert np.linalg.norm(Xg[:, l] - Xo[:, l]) <= 1e-6 * np.linalg.norm(Xo[:, l])
 
 
+@pytest.mark.parametrize("m", [1, 3, 6, 12])
+@pytest.mark.parametrize("precond", ["chebyshev", "amg"])
+def test_mixed_precision_widths(ens, m, precond):
+    """Mixed solves at widths that take each float32 column mapping of the inner solver: one column
+    (m = 1), four per lane with a padding column (m = 3 -> 4), two per lane (m = 6), four per lane
+    over four lanes (m = 12); true FP64 residual <= tol and the oracle's FP64 solution to 1e-6."""
+    op = gen.channel(24, 16, 12)
+    B = gen.rhs_normal(op.n, m, 90 + m, zero_mean=True)
+    with ens.Matrix.from_operator(op) as A:
+        if precond == "amg":
+            A.amg_setup()
+        X, st = ens.solve_block(A, torch.from_numpy(B).cuda(), tol=1e-10, precond=precond, precision="mixed")
+        Xg = X.cpu().numpy()
+    assert (st["status"] == 0).all(), st
+    assert np.all(_true_relres(op, B, Xg) <= 1.05e-10)
+    Xo, _, _, st_o = oracle.solve_block(op, B, 1e-12, precond="chebyshev")
+    assert (st_o == 0).all()
+    for l in range(m):
+        assert np.linalg.norm(Xg[:, l] - Xo[:, l]) <= 1e-6 * np.linalg.norm(Xo[:, l]), l
+
+
 def test_statuses_match_oracle(ens):
     op = gen.channel(16, 12, 8)
     n = op.n
