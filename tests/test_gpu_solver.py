@@ -1,6 +1,6 @@
 """Multi-RHS BiCGStab through the C ABI (ens_solve_block) against the CPU oracle.
 
-Bars (the benchmark spec): every column reaches relative residual <= tol (1e-8 unless stated; checked by
+Bars: every column reaches relative residual <= tol (1e-8 unless stated; checked by
 the library's reported true residual AND independently by the oracle's SpMV on the returned
 solution), and the solution matches the oracle's FP64 solution to 1e-6 relative (after mean
 removal for singular operators). Iteration counts may differ slightly (different rounding and
