@@ -1090,16 +1090,37 @@ struct Bicg {
   // whose condition (some column active and fewer than max_iter iterations) is set on the device
   // by k_loop_cond; one graph launch runs the whole solve with no host round trip. The loop ends
   // after at most max_iter iterations.
-  cudaError_t iterate_graph(T *x, int max_iter, int *ran) {
-    *ran = 0;
-    if (max_iter <= 0) return cudaSuccess;
+  //
+  // The instantiated loop is kept and replayed by later calls on the same x and max_iter (the mixed
+  // solver's outer steps rerun the same inner loop on the same buffers; every value that changes
+  // between them lives in device memory), so it is captured and instantiated once per solve.
+  struct LoopGraph {
     cudaStream_t cap = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+    const void *x = nullptr;
+    int max_iter = 0;
+    LoopGraph() = default;
+    LoopGraph(const LoopGraph &) = delete;
+    LoopGraph &operator=(const LoopGraph &) = delete;
+    ~LoopGraph() { release(); }
+    void release() {
+      if (ge) cudaGraphExecDestroy(ge);
+      if (g) cudaGraphDestroy(g);
+      if (cap) cudaStreamDestroy(cap);
+      ge = nullptr;
+      g = nullptr;
+      cap = nullptr;
+      x = nullptr;
+    }
+  } loop;
+
+  cudaError_t build_loop(T *x, int max_iter) {
+    loop.release();
+    cudaError_t e = cudaStreamCreateWithFlags(&loop.cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&loop.g, 0);
     cudaGraphConditionalHandle h{};
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, loop.g, 1, cudaGraphCondAssignDefault);
     cudaGraph_t body = nullptr;
     if (e == cudaSuccess) {
       cudaGraphNodeParams np = {};
@@ -1108,29 +1129,41 @@ struct Bicg {
       np.conditional.type = cudaGraphCondTypeWhile;
       np.conditional.size = 1;
       cudaGraphNode_t node;
-      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+      e = cudaGraphAddNode(&node, loop.g, nullptr, nullptr, 0, &np);
       if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(loop.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t ek = iteration(x, max_iter, cap);
+      cudaError_t ek = iteration(x, max_iter, loop.cap);
       if (ek == cudaSuccess) {
-        k_loop_cond<<<1, 32, 0, cap>>>(h, cs.it);
+        k_loop_cond<<<1, 32, 0, loop.cap>>>(h, cs.it);
         ek = cudaGetLastError();
       }
       cudaGraph_t captured = nullptr;
-      e = cudaStreamEndCapture(cap, &captured);
+      e = cudaStreamEndCapture(loop.cap, &captured);
       if (e == cudaSuccess) e = ek;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&loop.ge, loop.g, 0);
+    if (e == cudaSuccess) {
+      loop.x = x;
+      loop.max_iter = max_iter;
+    } else {
+      loop.release();
+    }
+    return e;
+  }
+
+  cudaError_t iterate_graph(T *x, int max_iter, int *ran) {
+    *ran = 0;
+    if (max_iter <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!loop.ge || loop.x != x || loop.max_iter != max_iter) e = build_loop(x, max_iter);
     // skip the launch when every column finished in the start phase
     std::vector<int32_t> st;
     if (e == cudaSuccess) e = states(st);
-    if (e == cudaSuccess && !all_done(st)) e = cudaGraphLaunch(ge, s);
+    if (e == cudaSuccess && !all_done(st)) e = cudaGraphLaunch(loop.ge, s);
     if (e == cudaSuccess) e = iterations_run(ran);
-    if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
-    if (cap) cudaStreamDestroy(cap);
     return e;
   }
 
