@@ -108,12 +108,13 @@ def test_mixed_precision_matches_fp64_oracle(ens, precond):
         assert np.linalg.norm(Xg[:, l] - Xo[:, l]) <= 1e-6 * np.linalg.norm(Xo[:, l])
 
 
-@pytest.mark.parametrize("m", [1, 3, 6, 12])
+@pytest.mark.parametrize("m", [1, 3, 6, 12, 33, 64])
 @pytest.mark.parametrize("precond", ["chebyshev", "amg"])
 def test_mixed_precision_widths(ens, m, precond):
     """Mixed solves at widths that take each float32 column mapping of the inner solver: one column
     (m = 1), four per lane with a padding column (m = 3 -> 4), two per lane (m = 6), four per lane
-    over four lanes (m = 12); true FP64 residual <= tol and the oracle's FP64 solution to 1e-6."""
+    over four lanes (m = 12), two per lane over 32 lanes (m = 33 -> 34), four per lane over 16 lanes
+    (m = 64, the widest); true FP64 residual <= tol and the oracle's FP64 solution to 1e-6."""
     op = gen.channel(24, 16, 12)
     B = gen.rhs_normal(op.n, m, 90 + m, zero_mean=True)
     with ens.Matrix.from_operator(op) as A:
