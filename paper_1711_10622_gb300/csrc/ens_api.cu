@@ -83,6 +83,10 @@ void free_matrix(ens_matrix *A) {
   cudaFree(A->stage_x);
   cudaFree(A->stage_y);
   cudaFree(A->ws);
+  for (cudaEvent_t ev : A->pipe_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (A->pipe_h2d) cudaStreamDestroy(A->pipe_h2d);
+  if (A->pipe_d2h) cudaStreamDestroy(A->pipe_d2h);
   delete A;
 }
 
@@ -175,6 +179,21 @@ ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, con
   }
   A->split_ok = (hflags & 1u) == 0;
   A->full_diag = (hflags & 2u) == 0;
+  // Row chunks of the pipelined host-buffer product: up to kPipeChunks chunks of whole tiles, each
+  // with the prefix maximum of its column indices (the X rows it needs).
+  {
+    const int64_t tiles = (n + kPipeAlignRows - 1) / kPipeAlignRows;
+    const int64_t chunks = std::min<int64_t>(kPipeChunks, tiles);
+    const int64_t per = (tiles + chunks - 1) / chunks * kPipeAlignRows;
+    int64_t need = 0;
+    for (int64_t r0 = 0; r0 < n; r0 += per) {
+      const int64_t r1 = std::min<int64_t>(n, r0 + per);
+      for (int64_t j = row_ptr[r0]; j < row_ptr[r1]; ++j) need = std::max<int64_t>(need, (int64_t)col_idx[j] + 1);
+      A->pipe_row.push_back(r0);
+      A->pipe_need.push_back(need);
+    }
+    A->pipe_row.push_back(n);
+  }
   *out = A;
   return ENS_OK;
 }
@@ -252,11 +271,61 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
     }
     A->stage_bytes = bytes;
   }
-  ENS_CUDA_TRY(cudaMemcpyAsync(A->stage_x, X, bytes, cudaMemcpyHostToDevice, s));
-  ens_status st = launch_gspmv(A, m, dtype, A->stage_x, A->stage_y, s);
+  const int64_t chunks = (int64_t)A->pipe_row.size() - 1;
+  if (chunks < 2) {
+    ENS_CUDA_TRY(cudaMemcpyAsync(A->stage_x, X, bytes, cudaMemcpyHostToDevice, s));
+    ens_status st = launch_gspmv(A, m, dtype, A->stage_x, A->stage_y, s);
+    if (st != ENS_OK) return st;
+    ENS_CUDA_TRY(cudaMemcpyAsync(Y, A->stage_y, bytes, cudaMemcpyDeviceToHost, s));
+    ENS_CUDA_TRY(cudaStreamSynchronize(s));
+    return ENS_OK;
+  }
+  // Pipelined: X arrives in prefixes on one copy stream, each row chunk runs on `s` once the
+  // prefix it reads is in, and its Y rows leave on a second copy stream (both copy directions and
+  // the kernels overlap).
+  cudaError_t e = cudaSuccess;
+  if (!A->pipe_h2d) {
+    e = cudaStreamCreateWithFlags(&A->pipe_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->pipe_d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) A->pipe_ev.assign(2 * chunks + 1, nullptr);
+    for (cudaEvent_t &ev : A->pipe_ev)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "gspmv_host pipeline set-up");
+  }
+  const size_t row_bytes = (size_t)m * (dtype == ENS_F64 ? 8 : 4);
+  const char *hx = (const char *)X;
+  char *hy = (char *)Y, *dx = (char *)A->stage_x, *dy = (char *)A->stage_y;
+  cudaEvent_t *ev_x = A->pipe_ev.data(), *ev_y = ev_x + chunks, ev_start = ev_x[2 * chunks];
+  e = cudaEventRecord(ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(A->pipe_h2d, ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(A->pipe_d2h, ev_start, 0);
+  int64_t have = 0;
+  for (int64_t k = 0; k < chunks && e == cudaSuccess; ++k) {
+    const int64_t need = A->pipe_need[k];
+    if (need > have)
+      e = cudaMemcpyAsync(dx + have * row_bytes, hx + have * row_bytes, (need - have) * row_bytes, cudaMemcpyHostToDevice,
+                          A->pipe_h2d);
+    have = std::max(have, need);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_x[k], A->pipe_h2d);
+  }
+  ens_status st = ENS_OK;
+  for (int64_t k = 0; k < chunks && e == cudaSuccess && st == ENS_OK; ++k) {
+    const int64_t r0 = A->pipe_row[k], r1 = A->pipe_row[k + 1];
+    e = cudaStreamWaitEvent(s, ev_x[k], 0);
+    if (e == cudaSuccess) st = launch_gspmv_rows(A, m, dtype, A->stage_x, A->stage_y, r0, r1, s);
+    if (e == cudaSuccess && st == ENS_OK) e = cudaEventRecord(ev_y[k], s);
+    if (e == cudaSuccess && st == ENS_OK) e = cudaStreamWaitEvent(A->pipe_d2h, ev_y[k], 0);
+    if (e == cudaSuccess && st == ENS_OK)
+      e = cudaMemcpyAsync(hy + r0 * row_bytes, dy + r0 * row_bytes, (r1 - r0) * row_bytes, cudaMemcpyDeviceToHost,
+                          A->pipe_d2h);
+  }
+  // wait for every copy that was issued (also on failure: they read and write the caller's buffers)
+  const cudaError_t e1 = cudaStreamSynchronize(A->pipe_h2d);
+  const cudaError_t e2 = cudaStreamSynchronize(A->pipe_d2h);
+  const cudaError_t e3 = cudaStreamSynchronize(s);
   if (st != ENS_OK) return st;
-  ENS_CUDA_TRY(cudaMemcpyAsync(Y, A->stage_y, bytes, cudaMemcpyDeviceToHost, s));
-  ENS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+  if (e != cudaSuccess) return cuda_fail(e, "gspmv_host");
   return ENS_OK;
 }
 

@@ -70,24 +70,35 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<Arith, VEC>::value)
   gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
 }
 
-int grid_for(const ens_matrix *A, const void *kernel) {
+// A contiguous range of rows [r0, r1) of the product (r0 a multiple of kTileRows, so the shifted
+// row-pointer array keeps its 16-byte alignment).
+struct Rows {
+  int64_t r0, r1;
+};
+static_assert(kPipeAlignRows % kTileRows == 0, "row chunks must be whole tiles");
+
+int grid_for(const ens_matrix *A, int64_t rows, const void *kernel) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (A->n + kTileRows - 1) / kTileRows;
+  const int64_t need = (rows + kTileRows - 1) / kTileRows;
   const int64_t full = (int64_t)A->num_sms * per_sm;
   return (int)(need < full ? need : full);
 }
 
 template <typename Arith, int VEC, int LANES>
-cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, cudaStream_t s) {
+cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, const Rows &rows, cudaStream_t s) {
   using T = typename Arith::T;
+  MatView v = view_of(A);
+  v.n = (int32_t)(rows.r1 - rows.r0);
+  v.rp = A->row + rows.r0;
+  T *y = (T *)Y + rows.r0 * m;
   if constexpr (std::is_same<Arith, ArithF64Split>::value || std::is_same<Arith, ArithF32>::value) {
     auto k = gspmv_kernel_capped<Arith, VEC, LANES>;
-    k<<<grid_for(A, (const void *)k), kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
+    k<<<grid_for(A, v.n, (const void *)k), kThreads, 0, s>>>(v, m, (const T *)X, y, mask);
   } else {
     auto k = gspmv_kernel<Arith, VEC, LANES>;
-    k<<<grid_for(A, (const void *)k), kThreads, 0, s>>>(view_of(A), m, (const T *)X, (T *)Y, mask);
+    k<<<grid_for(A, v.n, (const void *)k), kThreads, 0, s>>>(v, m, (const T *)X, y, mask);
   }
   return cudaGetLastError();
 }
@@ -102,14 +113,15 @@ bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 // Dispatch on LANES, a power of two in [1, 32].
 template <typename Arith, int VEC>
-cudaError_t dispatch(const ens_matrix *A, int m, const void *X, void *Y, int lanes, uint32_t mask, cudaStream_t s) {
+cudaError_t dispatch(const ens_matrix *A, int m, const void *X, void *Y, int lanes, uint32_t mask, const Rows &rows,
+                     cudaStream_t s) {
   switch (lanes) {
-    case 1: return run<Arith, VEC, 1>(A, m, X, Y, mask, s);
-    case 2: return run<Arith, VEC, 2>(A, m, X, Y, mask, s);
-    case 4: return run<Arith, VEC, 4>(A, m, X, Y, mask, s);
-    case 8: return run<Arith, VEC, 8>(A, m, X, Y, mask, s);
-    case 16: return run<Arith, VEC, 16>(A, m, X, Y, mask, s);
-    default: return run<Arith, VEC, 32>(A, m, X, Y, mask, s);
+    case 1: return run<Arith, VEC, 1>(A, m, X, Y, mask, rows, s);
+    case 2: return run<Arith, VEC, 2>(A, m, X, Y, mask, rows, s);
+    case 4: return run<Arith, VEC, 4>(A, m, X, Y, mask, rows, s);
+    case 8: return run<Arith, VEC, 8>(A, m, X, Y, mask, rows, s);
+    case 16: return run<Arith, VEC, 16>(A, m, X, Y, mask, rows, s);
+    default: return run<Arith, VEC, 32>(A, m, X, Y, mask, rows, s);
   }
 }
 
@@ -194,24 +206,25 @@ Cfg default_cfg(const ens_matrix *A, int m, int dtype, const void *X, const void
   return c;
 }
 
-cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, void *Y, const Cfg &c, cudaStream_t s) {
+cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, void *Y, const Cfg &c, const Rows &rows,
+                       cudaStream_t s) {
   if (dtype == ENS_F32) {
-    if (c.vec == 4) return dispatch<ArithF32, 4>(A, m, X, Y, c.lanes, 0u, s);
-    if (c.vec == 2) return dispatch<ArithF32, 2>(A, m, X, Y, c.lanes, 0u, s);
-    return dispatch<ArithF32, 1>(A, m, X, Y, c.lanes, 0u, s);
+    if (c.vec == 4) return dispatch<ArithF32, 4>(A, m, X, Y, c.lanes, 0u, rows, s);
+    if (c.vec == 2) return dispatch<ArithF32, 2>(A, m, X, Y, c.lanes, 0u, rows, s);
+    return dispatch<ArithF32, 1>(A, m, X, Y, c.lanes, 0u, rows, s);
   }
   if (c.share == kShareHybrid) {  // column hybrid needs two columns per lane
-    return c.vec == 2 ? dispatch<ArithF64Hybrid, 2>(A, m, X, Y, c.lanes, 0u, s)
-                      : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, s);
+    return c.vec == 2 ? dispatch<ArithF64Hybrid, 2>(A, m, X, Y, c.lanes, 0u, rows, s)
+                      : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, rows, s);
   }
   if (c.share < 32) {
     const uint32_t mask = share_mask(c.share);
-    if (c.vec == 4) return dispatch<ArithF64Split, 4>(A, m, X, Y, c.lanes, mask, s);
-    return c.vec == 2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, c.lanes, mask, s)
-                      : dispatch<ArithF64Split, 1>(A, m, X, Y, c.lanes, mask, s);
+    if (c.vec == 4) return dispatch<ArithF64Split, 4>(A, m, X, Y, c.lanes, mask, rows, s);
+    return c.vec == 2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, c.lanes, mask, rows, s)
+                      : dispatch<ArithF64Split, 1>(A, m, X, Y, c.lanes, mask, rows, s);
   }
-  return c.vec == 2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, c.lanes, 0u, s)
-                    : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, s);
+  return c.vec == 2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, c.lanes, 0u, rows, s)
+                    : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, rows, s);
 }
 
 // Deterministic N(0,1)-like fill of the tuning block (values in the split range, no zeros).
@@ -233,7 +246,16 @@ __global__ void k_tune_fill(int64_t count, double *x, float *x32) {
 ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s) {
   if (A->n == 0) return ENS_OK;
   const Cfg c = default_cfg(A, m, dtype, X, Y);
-  cudaError_t e = launch_cfg(A, m, dtype, X, Y, c, s);
+  cudaError_t e = launch_cfg(A, m, dtype, X, Y, c, Rows{0, A->n}, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gspmv launch");
+  return ENS_OK;
+}
+
+ens_status launch_gspmv_rows(const ens_matrix *A, int m, int dtype, const void *X, void *Y, int64_t r0, int64_t r1,
+                             cudaStream_t s) {
+  if (r1 <= r0) return ENS_OK;
+  const Cfg c = default_cfg(A, m, dtype, X, Y);
+  cudaError_t e = launch_cfg(A, m, dtype, X, Y, c, Rows{r0, r1}, s);
   if (e != cudaSuccess) return cuda_fail(e, "gspmv launch");
   return ENS_OK;
 }
@@ -283,9 +305,9 @@ ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *la
   Cfg bestc = base;
   for (const Cfg &c : cand) {
     if (e != cudaSuccess) break;
-    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_cfg(A, m, dtype, X, Y, c, s);
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_cfg(A, m, dtype, X, Y, c, Rows{0, A->n}, s);
     if (e == cudaSuccess) e = cudaEventRecord(t0, s);
-    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_cfg(A, m, dtype, X, Y, c, s);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_cfg(A, m, dtype, X, Y, c, Rows{0, A->n}, s);
     if (e == cudaSuccess) e = cudaEventRecord(t1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     float ms = 0.f;

@@ -195,6 +195,23 @@ def test_gspmv_host_buffers(ens):
             _check_f32(op, X, Y)
 
 
+@pytest.mark.parametrize("m,dt", [(1, np.float64), (8, np.float64), (32, np.float64), (5, np.float64), (8, np.float32)])
+def test_gspmv_host_pipelined(ens, m, dt):
+    """ens_gspmv_host on an operator of 140 tiles: X arrives in prefixes, 8 row chunks run as their
+    prefixes land and their Y rows are copied out while later chunks compute; every row against
+    the definition (FP64 bound 1e-12 of |A||X|, FP32 bound (L+2) 2^-24)."""
+    op = _op("cubes48x32x24")
+    X = gen.rhs_normal(op.n, m, 600 + m).astype(dt)
+    with ens.Matrix.from_operator(op) as A:
+        Y = ens.gspmv_host(A, X)
+        Y2 = ens.gspmv_host(A, X)  # the pipeline's streams and events are reused
+    assert np.array_equal(Y, Y2)
+    if dt == np.float64:
+        _check_f64(op, X, Y)
+    else:
+        _check_f32(op, X, Y)
+
+
 def test_invalid_arguments(ens):
     op = _op("dirichlet12")
     with ens.Matrix.from_operator(op) as A:
