@@ -290,7 +290,15 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
     if (e == cudaSuccess) A->pipe_ev.assign(2 * chunks + 1, nullptr);
     for (cudaEvent_t &ev : A->pipe_ev)
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return cuda_fail(e, "gspmv_host pipeline set-up");
+    if (e != cudaSuccess) {  // leave no half-made pipeline behind: the next call starts over
+      for (cudaEvent_t ev : A->pipe_ev)
+        if (ev) cudaEventDestroy(ev);
+      A->pipe_ev.clear();
+      if (A->pipe_h2d) cudaStreamDestroy(A->pipe_h2d);
+      if (A->pipe_d2h) cudaStreamDestroy(A->pipe_d2h);
+      A->pipe_h2d = A->pipe_d2h = nullptr;
+      return cuda_fail(e, "gspmv_host pipeline set-up");
+    }
   }
   const size_t row_bytes = (size_t)m * (dtype == ENS_F64 ? 8 : 4);
   const char *hx = (const char *)X;
