@@ -71,6 +71,28 @@ def test_vcycle_parity(ens, name, m):
     assert np.all(np.abs(Z32 - ref).max(axis=0) <= 1e-4 * scale)
 
 
+def test_vcycle_fp32_views(ens):
+    """ens_amg_apply on float32 blocks that are 8- but not 16-byte aligned takes two columns per lane
+    (16-byte aligned blocks take four): both match the oracle's V-cycle."""
+    op = OPS["cubes48x32x24"]()
+    H = _oracle_amg(op)
+    m = 8
+    R = gen.rhs_normal(op.n, m, 45)
+    ref = H.vcycle(R.astype(np.float32).astype(np.float64))
+    scale = np.abs(ref).max(axis=0)
+    with ens.Matrix.from_operator(op) as A:
+        A.amg_setup(**AMG)
+        buf = torch.zeros(op.n * m + 2, dtype=torch.float32, device="cuda")
+        Rv = buf[2:].view(op.n, m)  # 8-byte aligned, not 16
+        Rv.copy_(torch.from_numpy(R.astype(np.float32)))
+        zbuf = torch.zeros(op.n * m + 2, dtype=torch.float32, device="cuda")
+        Zv = zbuf[2:].view(op.n, m)
+        ens.amg_apply(A, Rv, Zv)
+        Za = ens.amg_apply(A, torch.from_numpy(R.astype(np.float32)).cuda())
+    for Z in (Zv.cpu().numpy(), Za.cpu().numpy()):
+        assert np.all(np.abs(Z - ref).max(axis=0) <= 1e-4 * scale)
+
+
 @pytest.mark.parametrize("name", list(OPS))
 def test_solve_with_amg_matches_oracle(ens, name):
     op = OPS[name]()
