@@ -129,7 +129,8 @@ ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *
  * stream, each row chunk is computed on `stream` once the X rows its column indices reach have
  * arrived, and its Y rows are copied back on a second library-owned stream. Y holds the same
  * values as ens_gspmv's to within the accuracy bound below (the FP64 split/native assignment of
- * rows can differ with the chunking).
+ * rows can differ with the chunking). X and Y may overlap (an in-place product): the stages then
+ * run one after the other.
  */
 ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream);
 

@@ -272,7 +272,11 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
     A->stage_bytes = bytes;
   }
   const int64_t chunks = (int64_t)A->pipe_row.size() - 1;
-  if (chunks < 2) {
+  // X and Y may be the same host array (an in-place product): then all of X is copied in before
+  // any row of Y is copied out
+  const char *xb = (const char *)X, *yb = (const char *)Y;
+  const bool overlap = xb < yb + bytes && yb < xb + bytes;
+  if (chunks < 2 || overlap) {
     ENS_CUDA_TRY(cudaMemcpyAsync(A->stage_x, X, bytes, cudaMemcpyHostToDevice, s));
     ens_status st = launch_gspmv(A, m, dtype, A->stage_x, A->stage_y, s);
     if (st != ENS_OK) return st;

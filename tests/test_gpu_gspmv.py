@@ -212,6 +212,18 @@ def test_gspmv_host_pipelined(ens, m, dt):
         _check_f32(op, X, Y)
 
 
+def test_gspmv_host_in_place(ens):
+    """ens_gspmv_host with Y the same host array as X: the input is fully read before any output
+    row is written back."""
+    op = _op("cubes48x32x24")
+    m = 8
+    X = gen.rhs_normal(op.n, m, 610)
+    buf = X.copy()
+    with ens.Matrix.from_operator(op) as A:
+        ens.gspmv_host(A, buf, buf)
+    _check_f64(op, X, buf)
+
+
 def test_invalid_arguments(ens):
     op = _op("dirichlet12")
     with ens.Matrix.from_operator(op) as A:
