@@ -1,11 +1,12 @@
 // GSpMV Y = A X for a CSR matrix and an n x m row-interleaved block (Section 2.3, Fig. GSpMV).
 //
 // Work mapping: a "row group" of LANES consecutive threads owns one row at a time; each lane
-// owns VEC consecutive columns of that row and reads them from X with one VEC-wide load
-// (128-bit for double2 / float4), so a row of X (m contiguous values) is read by the group as
-// one contiguous segment. Every val[j] and col_idx[j] is loaded once per lane group and reused
-// for all the lane's columns; with LANES = m / VEC there is exactly one pass per row. The grid
-// is sized to fill the GPU once and strides over the rows.
+// owns VEC consecutive columns of that row and reads them from X with 16-byte loads (one double2
+// or float4; four doubles as two double2), so a row of X (m contiguous values) is read by the
+// group as one contiguous segment. Every val[j] and col_idx[j] is loaded once per lane group and
+// reused for all the lane's columns; with LANES = m / VEC there is exactly one pass per row. The
+// grid is sized to fill the GPU once and strides over tiles of rows; a launch may also cover a
+// row range only (the pipelined host-buffer product).
 //
 // Three arithmetic variants:
 //   * float32 (ENS_F32): float products and sums (inner solver of the mixed-precision mode).
