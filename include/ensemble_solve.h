@@ -127,7 +127,9 @@ ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *
  * Y is written). Page-locked host memory gives the full copy bandwidth. On matrices of more than
  * one 256-row tile the three stages overlap: X arrives in row prefixes on a library-owned copy
  * stream, each row chunk is computed on `stream` once the X rows its column indices reach have
- * arrived, and its Y rows are copied back on a second library-owned stream. Y holds the same
+ * arrived, and its Y rows are copied back on a second library-owned stream. The overlap needs
+ * page-locked X and Y: with pageable buffers each copy call returns only when it is done, so the
+ * copies and kernels then run largely one after another. Y holds the same
  * values as ens_gspmv's to within the accuracy bound below (the FP64 split/native assignment of
  * rows can differ with the chunking). X and Y may overlap (an in-place product): the stages then
  * run one after the other.
@@ -141,12 +143,16 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
  * that cannot afford an allocation's latency or implicit synchronisation, and hosts that forbid
  * plug-in libraries from allocating. It calls no cudaMalloc, cudaFree or other allocating routine:
  * X and Y are staged through one array compiled into the library, 2 x 16 MiB, which every GPU that
- * loads the library holds until the process exits.
+ * loads the array holds until the process exits.
  *   Same arguments, semantics and accuracy as ens_gspmv_host (host X read, host Y written;
  *   synchronous). n * m * sizeof(dtype) must not exceed 16 MiB (16,777,216 bytes; e.g. n*m <= 2,097,152
  *   for float64); larger requests return ENS_ERR_INVALID. The matrix's device must be current.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *   device current; make that first call before any stream capture.
+ *   device current. With CUDA's lazy module loading (the default since CUDA 12.2) that lookup is
+ *   also what loads the array's module, so the 32 MiB (plus a small module overhead) are reserved on
+ *   the device by that FIRST call, not when the library is loaded. Make the first call once per
+ *   device at start-up: before the application reserves its own device-memory pool, and before any
+ *   stream capture. Every later call reserves nothing.
  *   All calls share the array and it keeps the last call's contents; nothing in it needs to start at
  *   zero (each call overwrites the staged X and all of Y). Calls whose GPU work overlapped would race
  *   on it; this entry point serialises its callers with a lock and returns only after its own copies

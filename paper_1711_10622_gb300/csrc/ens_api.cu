@@ -278,10 +278,15 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
   const bool overlap = xb < yb + bytes && yb < xb + bytes;
   if (chunks < 2 || overlap) {
     ENS_CUDA_TRY(cudaMemcpyAsync(A->stage_x, X, bytes, cudaMemcpyHostToDevice, s));
+    // every exit after the first copy waits for the stream: a later call may free and regrow
+    // the staging buffers, which must not happen under a copy or kernel still in flight
     ens_status st = launch_gspmv(A, m, dtype, A->stage_x, A->stage_y, s);
+    cudaError_t e = cudaSuccess;
+    if (st == ENS_OK) e = cudaMemcpyAsync(Y, A->stage_y, bytes, cudaMemcpyDeviceToHost, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
     if (st != ENS_OK) return st;
-    ENS_CUDA_TRY(cudaMemcpyAsync(Y, A->stage_y, bytes, cudaMemcpyDeviceToHost, s));
-    ENS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) return cuda_fail(e, "gspmv_host");
     return ENS_OK;
   }
   // Pipelined: X arrives in prefixes on one copy stream, each row chunk runs on `s` once the
@@ -320,14 +325,21 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
     have = std::max(have, need);
     if (e == cudaSuccess) e = cudaEventRecord(ev_x[k], A->pipe_h2d);
   }
+  // All chunk kernels are queued before any device-to-host copy: with pageable Y a copy call
+  // returns only when it is done, which would otherwise hold back the next chunk's launch.
   ens_status st = ENS_OK;
+  int64_t launched = 0;
   for (int64_t k = 0; k < chunks && e == cudaSuccess && st == ENS_OK; ++k) {
     const int64_t r0 = A->pipe_row[k], r1 = A->pipe_row[k + 1];
     e = cudaStreamWaitEvent(s, ev_x[k], 0);
     if (e == cudaSuccess) st = launch_gspmv_rows(A, m, dtype, A->stage_x, A->stage_y, r0, r1, s);
     if (e == cudaSuccess && st == ENS_OK) e = cudaEventRecord(ev_y[k], s);
-    if (e == cudaSuccess && st == ENS_OK) e = cudaStreamWaitEvent(A->pipe_d2h, ev_y[k], 0);
-    if (e == cudaSuccess && st == ENS_OK)
+    if (e == cudaSuccess && st == ENS_OK) launched = k + 1;
+  }
+  for (int64_t k = 0; k < launched && e == cudaSuccess; ++k) {
+    const int64_t r0 = A->pipe_row[k], r1 = A->pipe_row[k + 1];
+    e = cudaStreamWaitEvent(A->pipe_d2h, ev_y[k], 0);
+    if (e == cudaSuccess)
       e = cudaMemcpyAsync(hy + r0 * row_bytes, dy + r0 * row_bytes, (r1 - r0) * row_bytes, cudaMemcpyDeviceToHost,
                           A->pipe_d2h);
   }

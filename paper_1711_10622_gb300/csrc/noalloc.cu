@@ -61,9 +61,14 @@ extern "C" ens_status ens_gspmv_host_noalloc(const ens_matrix *A, int32_t m, int
   unsigned char *stage_y = stage_x + kNoAllocStageBytes;
   // Nothing has to start at zero: the copy overwrites the X part and the kernel writes all of Y.
   ENS_CUDA_TRY(cudaMemcpyAsync(stage_x, X, bytes, cudaMemcpyHostToDevice, s));
+  // From here on work on the shared array may be queued: every exit waits for the stream while
+  // the lock is still held, so the next caller never overwrites the array under running work.
   ens_status st = launch_gspmv(A, m, dtype, stage_x, stage_y, s);
+  cudaError_t e = cudaSuccess;
+  if (st == ENS_OK) e = cudaMemcpyAsync(Y, stage_y, bytes, cudaMemcpyDeviceToHost, s);
+  const cudaError_t es = cudaStreamSynchronize(s);
   if (st != ENS_OK) return st;
-  ENS_CUDA_TRY(cudaMemcpyAsync(Y, stage_y, bytes, cudaMemcpyDeviceToHost, s));
-  ENS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(e, "gspmv_host_noalloc");
   return ENS_OK;
 }

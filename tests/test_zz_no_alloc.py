@@ -51,6 +51,26 @@ def _noalloc(ens, A, X, Y):
     return st
 
 
+def test_noalloc_first_call_reserves_only_the_array(ens):
+    """The first call on a device loads the array's module (lazy module loading) and so reserves the
+    2 x 16 MiB staging array; later calls reserve nothing. Runs before any other call in this file."""
+    op = gen.dirichlet_box(16)
+    with ens.Matrix.from_operator(op) as A:
+        X = gen.rhs_normal(op.n, 4, 13)
+        ens.gspmv_host(A, X)  # load the product kernels' module and the allocating path's buffers first
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        Y = np.empty_like(X)
+        assert _noalloc(ens, A, X, Y) == 0
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free0 - free1 <= (32 << 20) + (8 << 20), (free0 - free1) / 2**20
+        for _ in range(3):
+            assert _noalloc(ens, A, X, Y) == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free1
+
+
 @pytest.mark.parametrize("dtype,m", [(np.float64, 8), (np.float32, 8), (np.float64, 3)])
 def test_noalloc_matches_allocating_entry_point(ens, dtype, m):
     op = gen.cubes(48, 32, 24, size=4)
