@@ -24,6 +24,7 @@ from . import estimates  # noqa: F401  (re-exported)
 CONVERGED, MAXITER, BREAKDOWN, NONFINITE, INCOMPATIBLE = 0, 1, 2, 3, 4
 
 _lib = None
+_lib_omp = None
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -41,31 +42,62 @@ class _Opts(ctypes.Structure):
     ]
 
 
+def _declare(L):
+    L.oracle_spmv.argtypes = [_i64, _vp, _vp, _vp, _vp, _i64, _vp, _i64]
+    L.oracle_gspmv.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+    L.oracle_chebyshev.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.oracle_bicgstab.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_Opts), _vp, _vp]
+    L.oracle_bicgstab.restype = ctypes.c_int
+    L.oracle_solve_block.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _vp]
+    L.oracle_lu_solve.argtypes = [ctypes.c_int, _vp, _vp]
+    L.oracle_lu_solve.restype = ctypes.c_int
+    L.oracle_amg_setup.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    L.oracle_amg_setup.restype = _vp
+    L.oracle_amg_free.argtypes = [_vp]
+    L.oracle_amg_levels.argtypes = [_vp, _vp, _vp]
+    L.oracle_amg_levels.restype = ctypes.c_int
+    L.oracle_amg_level.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.oracle_amg_vcycle.argtypes = [_vp, _vp, _vp]
+    grid_args = [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double]
+    L.oracle_divergence.argtypes = grid_args + [_vp, _vp, _vp, _vp]
+    L.oracle_grad_correct.argtypes = grid_args + [_vp, _vp, _vp, _vp]
+    L.oracle_gspmv_rowwise.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+    L.oracle_threads.restype = ctypes.c_int
+    return L
+
+
 def lib():
+    """The serial oracle (the test oracle)."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        L.oracle_spmv.argtypes = [_i64, _vp, _vp, _vp, _vp, _i64, _vp, _i64]
-        L.oracle_gspmv.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]
-        L.oracle_chebyshev.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        L.oracle_bicgstab.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_Opts), _vp, _vp]
-        L.oracle_bicgstab.restype = ctypes.c_int
-        L.oracle_solve_block.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _vp]
-        L.oracle_lu_solve.argtypes = [ctypes.c_int, _vp, _vp]
-        L.oracle_lu_solve.restype = ctypes.c_int
-        L.oracle_amg_setup.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
-        L.oracle_amg_setup.restype = _vp
-        L.oracle_amg_free.argtypes = [_vp]
-        L.oracle_amg_levels.argtypes = [_vp, _vp, _vp]
-        L.oracle_amg_levels.restype = ctypes.c_int
-        L.oracle_amg_level.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
-        L.oracle_amg_vcycle.argtypes = [_vp, _vp, _vp]
-        grid_args = [_i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double]
-        L.oracle_divergence.argtypes = grid_args + [_vp, _vp, _vp, _vp]
-        L.oracle_grad_correct.argtypes = grid_args + [_vp, _vp, _vp, _vp]
-        _lib = L
+        _lib = _declare(ctypes.CDLL(_build.build()))
     return _lib
+
+
+def lib_omp():
+    """The same sources built with OpenMP (all host cores; same results bit for bit), for the CPU
+    baseline; None if the compiler lacks OpenMP."""
+    global _lib_omp
+    if _lib_omp is None:
+        path = _build.build_omp()
+        if path is None:
+            return None
+        _lib_omp = _declare(ctypes.CDLL(path))
+    return _lib_omp
+
+
+def _pick(parallel):
+    if not parallel:
+        return lib()
+    L = lib_omp()
+    if L is None:
+        raise RuntimeError("the OpenMP build of the oracle is unavailable (gcc without -fopenmp)")
+    return L
+
+
+def threads(parallel: bool = True) -> int:
+    """Threads the (OpenMP) oracle uses: omp_get_max_threads(), 1 for the serial build."""
+    return int(_pick(parallel).oracle_threads())
 
 
 def _p(a: np.ndarray):
@@ -88,15 +120,29 @@ def spmv(A, x: np.ndarray) -> np.ndarray:
     return y
 
 
-def gspmv(A, X: np.ndarray) -> np.ndarray:
-    """Y = A X for an n x m row-interleaved block, column by column (Section 2.3)."""
+def gspmv(A, X: np.ndarray, parallel: bool = False) -> np.ndarray:
+    """Y = A X for an n x m row-interleaved block, column by column (Section 2.3). parallel: the
+    OpenMP build (rows split over the host cores; same bits)."""
     row, col, val = _csr(A)
     X = np.ascontiguousarray(X, dtype=np.float64)
     if X.ndim == 1:
         X = X[:, None]
     m = X.shape[1]
     Y = np.empty_like(X)
-    lib().oracle_gspmv(A.n, _p(row), _p(col), _p(val), m, _p(X), _p(Y))
+    _pick(parallel).oracle_gspmv(A.n, _p(row), _p(col), _p(val), m, _p(X), _p(Y))
+    return Y
+
+
+def gspmv_rowwise(A, X: np.ndarray, parallel: bool = False) -> np.ndarray:
+    """Y = A X with the m columns of each row together (the loop order of Fig. GSpMV); the same
+    bits as gspmv()."""
+    row, col, val = _csr(A)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    m = X.shape[1]
+    Y = np.empty_like(X)
+    _pick(parallel).oracle_gspmv_rowwise(A.n, _p(row), _p(col), _p(val), m, _p(X), _p(Y))
     return Y
 
 
@@ -192,9 +238,11 @@ def solve_block(
     cheb_hi=DEFAULT_CHEB_HI,
     cheb_steps=DEFAULT_CHEB_STEPS,
     amg=None,
+    parallel: bool = False,
 ):
     """m independent BiCGStab solves A x_l = b_l (Section 2.2 / 4.1); precond 'none', 'chebyshev'
-    or 'amg' (with amg = an oracle.AMG hierarchy of A).
+    or 'amg' (with amg = an oracle.AMG hierarchy of A). parallel: the OpenMP build (columns solved
+    on separate host cores; same bits).
 
     Returns (X, iters[m], relres[m], status[m]); relres is the true residual at exit.
     """
@@ -210,7 +258,8 @@ def solve_block(
     status = np.zeros(m, dtype=np.int32)
     sing = A.singular if singular is None else singular
     o = _opts(max_iter, precond, sing, cheb_lo, cheb_hi, cheb_steps, amg)
-    lib().oracle_solve_block(
+    L = _pick(parallel)
+    L.oracle_solve_block(
         n, _p(row), _p(col), _p(val), m, _p(B), _p(X), _p(tolv), ctypes.byref(o), _p(iters), _p(relres), _p(status)
     )
     return X, iters, relres, status

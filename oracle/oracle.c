@@ -20,13 +20,33 @@
  *                      for ONE right-hand side, right-preconditioned, x0 given.
  *   oracle_solve_block m independent BiCGStab solves, one per column (Section 2.2: m pressure
  *                      solves share the matrix; only the right-hand sides differ).
+ *   oracle_gspmv_rowwise  the same Y = A X with the column loop inside the row loop (the form of
+ *                      Fig. GSpMV); every element is summed in the same order, so the result is
+ *                      bit-identical to oracle_gspmv.
  *   oracle_lu_solve    dense LU with partial pivoting (textbook), used to pin the solver.
  * The aggregation multigrid preconditioner (precond 2) lives in amg.c.
+ *
+ * The same source builds twice: serially (the test oracle) and with -fopenmp (the CPU baseline
+ * timed on all host cores). The OpenMP pragmas split only independent work, rows of a product and
+ * columns of a block solve, and every value is computed by the same serial code in the same order,
+ * so both builds give the same bits.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads an OpenMP region of this build may use (1 in the serial build). */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* Per-column outcome codes; the CUDA library uses the same numeric values. */
 #define OR_CONVERGED 0
@@ -38,6 +58,7 @@
 /* Section 2.3, Fig. GSpMV, m = 1. X element k of the column lives at x[k*incx]. */
 void oracle_spmv(int64_t n, const int32_t *row, const int32_t *col, const double *val,
                  const double *x, int64_t incx, double *y, int64_t incy) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double sum = 0.0;
     for (int64_t j = row[i]; j < row[i + 1]; ++j) sum += val[j] * x[(int64_t)col[j] * incx];
@@ -49,6 +70,23 @@ void oracle_spmv(int64_t n, const int32_t *row, const int32_t *col, const double
 void oracle_gspmv(int64_t n, const int32_t *row, const int32_t *col, const double *val, int m,
                   const double *X, double *Y) {
   for (int l = 0; l < m; ++l) oracle_spmv(n, row, col, val, X + l, m, Y + l, m);
+}
+
+/* Section 2.3, Fig. GSpMV: Y = A X with the m columns of a row computed together; each matrix entry
+ * is read once per row and applied to the whole row of X. Element (i, l) is still the sum over j
+ * ascending from 0, as in oracle_gspmv. */
+void oracle_gspmv_rowwise(int64_t n, const int32_t *row, const int32_t *col, const double *val, int m,
+                          const double *X, double *Y) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double *y = Y + i * m;
+    for (int l = 0; l < m; ++l) y[l] = 0.0;
+    for (int64_t j = row[i]; j < row[i + 1]; ++j) {
+      const double a = val[j];
+      const double *x = X + (int64_t)col[j] * m;
+      for (int l = 0; l < m; ++l) y[l] += a * x[l];
+    }
+  }
 }
 
 static double dot(int64_t n, const double *a, const double *b) {
@@ -230,14 +268,15 @@ int oracle_bicgstab(int64_t n, const int32_t *row, const int32_t *col, const dou
 void oracle_solve_block(int64_t n, const int32_t *row, const int32_t *col, const double *val, int m,
                         const double *B, double *X, const double *tol, const oracle_opts *o,
                         int *iters, double *relres, int *status) {
-  double *b = (double *)malloc(sizeof(double) * n), *x = (double *)malloc(sizeof(double) * n);
+#pragma omp parallel for schedule(dynamic, 1)
   for (int l = 0; l < m; ++l) {
+    double *b = (double *)malloc(sizeof(double) * n), *x = (double *)malloc(sizeof(double) * n);
     for (int64_t i = 0; i < n; ++i) { b[i] = B[i * m + l]; x[i] = X[i * m + l]; }
     status[l] = oracle_bicgstab(n, row, col, val, b, x, tol[l], o, &iters[l], &relres[l]);
     for (int64_t i = 0; i < n; ++i) X[i * m + l] = x[i];
+    free(b);
+    free(x);
   }
-  free(b);
-  free(x);
 }
 
 /* Dense LU with partial pivoting on a row-major N x N matrix (overwritten); b is overwritten with

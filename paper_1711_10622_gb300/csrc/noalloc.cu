@@ -66,9 +66,9 @@ extern "C" ens_status ens_gspmv_host_noalloc(const ens_matrix *A, int32_t m, int
   ens_status st = launch_gspmv(A, m, dtype, stage_x, stage_y, s);
   cudaError_t e = cudaSuccess;
   if (st == ENS_OK) e = cudaMemcpyAsync(Y, stage_y, bytes, cudaMemcpyDeviceToHost, s);
-  const cudaError_t es = cudaStreamSynchronize(s);
+  const cudaError_t esync = cudaStreamSynchronize(s);
   if (st != ENS_OK) return st;
-  if (e == cudaSuccess) e = es;
+  if (e == cudaSuccess) e = esync;
   if (e != cudaSuccess) return cuda_fail(e, "gspmv_host_noalloc");
   return ENS_OK;
 }

@@ -40,7 +40,8 @@ bool use_split(const ens_matrix *A);
 namespace solver {
 
 enum : int32_t { ST_ACTIVE = 0, ST_HALF = 1, ST_DONE = 2 };
-enum : int32_t { FL_EARLY = 1, FL_ZERO_B = 2 };
+// FL_NOSTEP: the column broke down in its first iteration before x was updated (x is still x0).
+enum : int32_t { FL_EARLY = 1, FL_ZERO_B = 2, FL_NOSTEP = 4 };
 
 template <typename T>
 struct Cols {
@@ -263,6 +264,7 @@ __global__ void ENS_TILE_BOUNDS(Arith)
     if (rv == T(0) || !isfinite(al)) {  // breakdown; x keeps its last finite iterate
       cs.state[l] = ST_DONE;
       cs.status[l] = ENS_COL_BREAKDOWN;
+      if (cs.it[0] == 0) cs.flags[l] |= FL_NOSTEP;
       return;
     }
     cs.alpha[l] = al;
@@ -335,6 +337,7 @@ __global__ void ENS_TILE_BOUNDS(Arith)
     if (t2 == T(0) || !isfinite(om)) {  // breakdown before x is updated with a non-finite step
       cs.state[l] = ST_DONE;
       cs.status[l] = ENS_COL_BREAKDOWN;
+      if (cs.it[0] == 0) cs.flags[l] |= FL_NOSTEP;
       return;
     }
     cs.omega[l] = om;
@@ -536,6 +539,19 @@ __global__ void __launch_bounds__(kThreads)
     for (int q = 0; q < VEC; ++q) o[q] = (float)(rv[q] * sc[q]);
     store_vec<float, VEC>(r32 + i * m + c, o);
   }
+}
+
+// Mixed precision, after an inner solve: an inner solve that broke down in its first iteration,
+// before any update, returns d = 0 and leaves the outer residual as it was, so the next refinement
+// step would repeat it exactly. Such a column ends with BREAKDOWN (x keeps its current iterate),
+// as the FP64 solve of the same column does.
+static __global__ void k_inner_nostep(int32_t mp, Cols<double> outer, const int32_t *__restrict__ inner_status,
+                                      const int32_t *__restrict__ inner_flags) {
+  for (int l = threadIdx.x; l < mp; l += blockDim.x)
+    if (outer.state[l] == ST_ACTIVE && inner_status[l] == ENS_COL_BREAKDOWN && (inner_flags[l] & FL_NOSTEP)) {
+      outer.state[l] = ST_DONE;
+      outer.status[l] = ENS_COL_BREAKDOWN;
+    }
 }
 
 // x += ||r|| d for active outer columns (the FP64 correction step).
@@ -1259,11 +1275,14 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
           iters[l] += inner_it[l];
           outer[l] += 1;
         }
-      e = with_vl(O.vec, O.lanes, [&](auto Vc, auto Lc) {
-        constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
-        k_correct<V, L><<<O.grid, kThreads, 0, s>>>((int32_t)n, mp, x, d32, O.cs, I.cs.status);
-        return cudaGetLastError();
-      });
+      k_inner_nostep<<<1, 64, 0, s>>>(mp, O.cs, I.cs.status, I.cs.flags);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = with_vl(O.vec, O.lanes, [&](auto Vc, auto Lc) {
+          constexpr int V = decltype(Vc)::value, L = decltype(Lc)::value;
+          k_correct<V, L><<<O.grid, kThreads, 0, s>>>((int32_t)n, mp, x, d32, O.cs, I.cs.status);
+          return cudaGetLastError();
+        });
       if (e == cudaSuccess) e = O.outer_residual(b, x);
     }
     if (e == cudaSuccess) e = O.finish(b, x, singular);
@@ -1485,6 +1504,10 @@ struct SysImpl : SysBase {
           }
           if (ek == cudaSuccess) {
             k_accum<<<1, 64, 0, c>>>(mp, S.cs.state, I.cs.iters, iters_tot, outer_cnt);
+            ek = cudaGetLastError();
+          }
+          if (ek == cudaSuccess) {
+            k_inner_nostep<<<1, 64, 0, c>>>(mp, S.cs, I.cs.status, I.cs.flags);
             ek = cudaGetLastError();
           }
           if (ek == cudaSuccess)
