@@ -149,41 +149,162 @@ def replica_throughput(dist, seconds: float, units_per_step: float, steps: int, 
     return seconds, world * units_per_step * steps / seconds
 
 
+def host_info():
+    """Core count and CPU model of this host (recorded beside every CPU number)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": os.uname().machine}
+
+
 def cpu_baseline_sweep(op, seconds_cap: float = 30.0):
-    """The oracle (serial C, FP64) on the host: one full m-sweep on the full channel operator."""
+    """The oracle (C, FP64) on the host, as it stands: (i) the serial build on one core, column by
+    column, one full m-sweep on the full channel operator (capped at `seconds_cap`); (ii) the OpenMP
+    build of the same source on all host cores, column by column and with the columns of a row
+    together (the loop order of Fig. GSpMV), one full sweep each; (iii) the oracle's per-column
+    BiCGStab on the plain-method workload (32^3, m = 4, tol 1e-8), serial and all cores.
+    `value` is the fastest all-core product (GB/s of algorithmic bytes)."""
+    import gen
+    import oracle
+
+    n, nnz = op.n, op.nnz
+    Xs = {m: gen.rhs_normal(n, m, 20000 + m) for m in M_SWEEP}
+
+    def sweep(fn, cap=None):
+        total_bytes, total_t, done = 0, 0.0, []
+        for m in M_SWEEP:
+            t0 = time.perf_counter()
+            fn(Xs[m])
+            total_t += time.perf_counter() - t0
+            total_bytes += alg_bytes(n, nnz, m)
+            done.append(m)
+            if cap is not None and total_t > cap:
+                break
+        return total_bytes / total_t / 1e9, done, total_t
+
+    serial_gbs, serial_done, _ = sweep(lambda X: oracle.gspmv(op, X), seconds_cap)
+    out = {
+        "value": serial_gbs,
+        "unit": "GB/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"one FP64 GSpMV per m in {serial_done} on the full {WORKLOAD} operator (serial C oracle, column by column)",
+        "serial": {"gbs": serial_gbs, "cores": 1, "widths": serial_done},
+        "host": host_info(),
+    }
+    if oracle.lib_omp() is not None:
+        threads = oracle.threads(parallel=True)
+        col_gbs, _, _ = sweep(lambda X: oracle.gspmv(op, X, parallel=True))
+        row_gbs, _, _ = sweep(lambda X: oracle.gspmv_rowwise(op, X, parallel=True))
+        out.update(
+            {
+                "value": max(col_gbs, row_gbs),
+                "cores": threads,
+                "sample": f"one FP64 GSpMV per m in {list(M_SWEEP)} on the full {WORKLOAD} operator, OpenMP build of the "
+                f"oracle on {threads} threads (rows split; columns of a row together = {row_gbs:.2f} GB/s, column by column = "
+                f"{col_gbs:.2f} GB/s); the serial build on 1 core: {serial_gbs:.2f} GB/s",
+                "all_cores": {"threads": threads, "rowwise_gbs": row_gbs, "columnwise_gbs": col_gbs},
+            }
+        )
+    # oracle block solves: RHS-solves/s of the per-column BiCGStab on the plain-method workload
+    w = gen.WORKLOADS["dirichlet32_m4"]
+    dop = w["op"]()
+    B = w["rhs"](dop.n, 4)
+    solves = {}
+    for par in (False, True):
+        if par and oracle.lib_omp() is None:
+            continue
+        t0 = time.perf_counter()
+        _, it, _, st = oracle.solve_block(dop, B, w["tol"], parallel=par)
+        dt = time.perf_counter() - t0
+        solves["all_cores" if par else "serial"] = {"rhs_solves_per_s": 4 / dt, "seconds": dt, "threads": oracle.threads(par),
+                                                    "iters": it.tolist(), "converged": int((st == 0).sum())}
+    out["solves_dirichlet32_m4"] = solves
+    return out
+
+
+def oracle_references(level: str = "default") -> dict:
+    """FP64 oracle solutions that the bench's GPU results are compared with (run in a spawned process
+    on the host cores while the GPU sections run). Each entry: the oracle's X for the columns listed,
+    solved to a tolerance tighter than the GPU's (so its own error does not mask the GPU's):
+      dirichlet32_m4         all 4 columns, unpreconditioned, tol 1e-12
+      cubes192x128x96_m8     all 8 columns, oracle AMG preconditioner, tol 1e-11
+      batch                  64^3 all 4 columns; 128^3 and 96x160x96 column 0 (AMG, tol 1e-12);
+                             256x192x192 column 0 only with level 'full' (minutes on the host)
+      serving                the sampled requests (see serving_samples), AMG, tol 1e-12
+    """
     import numpy as np
 
     import gen
     import oracle
 
-    n, nnz = op.n, op.nnz
-    total_bytes, total_t = 0, 0.0
-    done = []
-    for m in M_SWEEP:
-        X = gen.rhs_normal(n, m, 20000 + m)
+    out, t_all = {}, time.perf_counter()
+    par = oracle.lib_omp() is not None
+    w = gen.WORKLOADS["dirichlet32_m4"]
+    op = w["op"]()
+    t0 = time.perf_counter()
+    X, it, rr, st = oracle.solve_block(op, w["rhs"](op.n, 4), 1e-12, parallel=par)
+    out["dirichlet32_m4"] = {"X": X, "cols": [0, 1, 2, 3], "tol": 1e-12, "precond": "none", "status": st.tolist(),
+                             "seconds": time.perf_counter() - t0}
+    w = gen.WORKLOADS["cubes192x128x96_m8"]
+    op = w["op"]()
+    t0 = time.perf_counter()
+    H = oracle.AMG(op)
+    X, it, rr, st = oracle.solve_block(op, w["rhs"](op.n, 8), 1e-11, precond="amg", amg=H, parallel=par)
+    H.close()
+    out["cubes192x128x96_m8"] = {"X": X, "cols": list(range(8)), "tol": 1e-11, "precond": "amg", "status": st.tolist(),
+                                 "seconds": time.perf_counter() - t0}
+    batch = {}
+    for i, (dims, m) in enumerate(BATCH_SPECS):
+        cols = list(range(m)) if dims == (64, 64, 64) else [0]
+        if dims == (256, 192, 192) and level != "full":
+            continue
+        op = gen.channel(*dims)
+        B = gen.rhs_normal(op.n, m, 10622 + 40 + i, zero_mean=True)[:, cols]
         t0 = time.perf_counter()
-        oracle.gspmv(op, X)
-        total_t += time.perf_counter() - t0
-        total_bytes += alg_bytes(n, nnz, m)
-        done.append(m)
-        if total_t > seconds_cap:
-            break
-        del X
-    _ = np
-    return {
-        "value": total_bytes / total_t / 1e9,
-        "unit": "GB/s",
-        "cores": 1,
-        "kind": "oracle",
-        "sample": f"one FP64 GSpMV per m in {done} on the full {WORKLOAD} operator (serial C oracle, column by column)",
-    }
+        H = oracle.AMG(op)
+        X, it, rr, st = oracle.solve_block(op, np.ascontiguousarray(B), 1e-12, precond="amg", amg=H, parallel=par)
+        H.close()
+        batch["x".join(map(str, dims))] = {"X": X, "cols": cols, "tol": 1e-12, "precond": "amg", "status": st.tolist(),
+                                           "seconds": time.perf_counter() - t0}
+    out["batch"] = batch
+    ops = gen.serving_operators()
+    serving = {}
+    for k, (name, B) in serving_samples(ops).items():
+        op = ops[name]
+        t0 = time.perf_counter()
+        H = oracle.AMG(op)
+        X, it, rr, st = oracle.solve_block(op, B, 1e-12, precond="amg", amg=H, parallel=par)
+        H.close()
+        serving[k] = {"X": X, "op": name, "tol": 1e-12, "status": st.tolist(), "seconds": time.perf_counter() - t0}
+    out["serving"] = serving
+    out["threads"] = oracle.threads(par)
+    out["seconds"] = time.perf_counter() - t_all
+    return out
 
 
-def solve_metrics(reps: int = 2):
+def rel_err_cols(X, Xref, cols) -> float:
+    """max over the listed columns of ||x_l - x_ref,l|| / ||x_ref,l|| (host arrays)."""
+    import numpy as np
+
+    X = np.asarray(X)[:, cols]
+    return float((np.linalg.norm(X - Xref, axis=0) / np.linalg.norm(Xref, axis=0)).max())
+
+
+def solve_metrics(reps: int = 2, keep: dict | None = None):
     """RHS-solves/s of the block solver against the one-RHS-at-a-time solver (the same library,
     m = 1, looped over the columns) on the configured solve workloads: against FP64 with the plain
     preconditioner, and like for like (same preconditioner and precision). Each solve is timed end to
-    end around the synchronous ens_solve_block call (inputs resident on the GPU)."""
+    end around the synchronous ens_solve_block call (inputs resident on the GPU). The solutions are
+    kept (host copies in `keep`) for the error against the oracle, attached once the oracle's
+    references are in. The cube workload also runs at tol 1e-9, where its solution error meets the
+    1e-6 bar (at 1e-8 the operator's conditioning leaves errors up to ~1e-5)."""
     import torch
 
     import gen
@@ -193,12 +314,14 @@ def solve_metrics(reps: int = 2):
         ("dirichlet32_m4", gen.WORKLOADS["dirichlet32_m4"], 4, "none"),
         ("cubes192x128x96_m8", gen.WORKLOADS["cubes192x128x96_m8"], 8, "chebyshev"),
     ]
+    keep = {} if keep is None else keep
     out = {}
     for name, w, m, pre in cases:
         op = w["op"]()
         B = torch.from_numpy(w["rhs"](op.n, m)).cuda()
         tol = w["tol"]
         A = ens.Matrix.from_operator(op)
+        kept = keep.setdefault(name, {})
 
         def timed(fn):
             fn()
@@ -213,38 +336,34 @@ def solve_metrics(reps: int = 2):
             return best, r
 
         res = {}
-        # reference solution for the error of every result: FP64 block solve to 1e-12
-        Xref, _ = ens.solve_block(A, B, tol=1e-12, precond="chebyshev" if pre == "chebyshev" else "none")
 
-        def rel_err(X):
-            return (torch.linalg.vector_norm(X - Xref, dim=0) / torch.linalg.vector_norm(Xref, dim=0)).max().item()
-
-        for prec in ("f64", "mixed"):
-            t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tol, precond=pre, precision=prec))
-            res[prec] = {
-                "max_rel_err_vs_fp64_1e-12": rel_err(X),
+        def record(key, t, X, st, tol_used):
+            kept[key] = X.cpu().numpy()
+            res[key] = {
                 "solves_per_s": m / t,
                 "seconds": t,
+                "tol": tol_used,
                 "max_relres": float(st["relres"].max()),
                 "converged": int((st["status"] == 0).sum()),
                 "iters": st["iters"].tolist(),
                 "outer": st["outer"].tolist(),
             }
+
+        tols = (tol, 1e-9) if pre == "chebyshev" else (tol,)
+        for tl in tols:
+            sfx = "" if tl == tol else "_tol1e-9"
+            for prec in ("f64", "mixed"):
+                t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tl, precond=pre, precision=prec))
+                record(prec + sfx, t, X, st, tl)
         if pre == "chebyshev":  # the same solves with the aggregation multigrid V-cycle instead
             t_setup = time.perf_counter()
             levels = A.amg_setup()
             t_setup = time.perf_counter() - t_setup
-            for prec in ("f64", "mixed"):
-                t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tol, precond="amg", precision=prec))
-                res[prec + "_amg"] = {
-                    "max_rel_err_vs_fp64_1e-12": rel_err(X),
-                    "solves_per_s": m / t,
-                    "seconds": t,
-                    "max_relres": float(st["relres"].max()),
-                    "converged": int((st["status"] == 0).sum()),
-                    "iters": st["iters"].tolist(),
-                    "outer": st["outer"].tolist(),
-                }
+            for tl in tols:
+                sfx = "" if tl == tol else "_tol1e-9"
+                for prec in ("f64", "mixed"):
+                    t, (X, st) = timed(lambda: ens.solve_block(A, B, tol=tl, precond="amg", precision=prec))
+                    record(prec + "_amg" + sfx, t, X, st, tl)
             res["amg_setup_s"] = t_setup
             res["amg_levels"] = levels
         # one-RHS-at-a-time baselines: the same solver with m = 1 looped over the columns, for every
@@ -253,6 +372,7 @@ def solve_metrics(reps: int = 2):
         for key in [k for k in ("f64", "mixed", "f64_amg", "mixed_amg") if k in res]:
             prec, _, p1 = key.partition("_")
             t1, outs = timed(lambda: [ens.solve_block(A, c, tol=tol, precond=p1 or pre, precision=prec) for c in cols])
+            kept["one_rhs_" + key] = torch.cat([o[0] for o in outs], dim=1).cpu().numpy()
             res["one_rhs_" + key] = {"solves_per_s": m / t1, "seconds": t1, "iters": [int(o[1]["iters"][0]) for o in outs]}
             res[key]["speedup_vs_one_rhs_same"] = res[key]["solves_per_s"] / res["one_rhs_" + key]["solves_per_s"]
         base = res["one_rhs_f64"]["solves_per_s"]
@@ -264,6 +384,22 @@ def solve_metrics(reps: int = 2):
         out[name] = res
         A.close()
     return out
+
+
+def attach_oracle_errors(section: dict, keep: dict, refs: dict, sol_bar: float = 1e-6):
+    """Add max_rel_err_vs_oracle to every kept result of `section` (per workload) from the oracle's
+    references; meets_1e-6 says whether the solution-error bar holds for that result."""
+    for name, kept in keep.items():
+        ref = refs.get(name)
+        if ref is None or name not in section:
+            continue
+        for key, X in kept.items():
+            err = rel_err_cols(X, ref["X"], ref["cols"])
+            entry = section[name].setdefault(key, {})
+            entry["max_rel_err_vs_oracle"] = err
+            entry["meets_1e-6"] = err <= sol_bar
+        section[name]["oracle_reference"] = {"tol": ref["tol"], "precond": ref["precond"], "columns": ref["cols"],
+                                             "host_seconds": ref["seconds"]}
 
 
 def cubes_gspmv_metrics(reps: int = 20):
@@ -299,21 +435,26 @@ def cubes_gspmv_metrics(reps: int = 20):
     return {"workload": "cubes192x128x96", "n": op.n, "nnz": op.nnz, "sweep": sweep}
 
 
-def batch_metrics(precond: str = "amg"):
+BATCH_SPECS = [((256, 192, 192), 16), ((64, 64, 64), 4), ((128, 128, 128), 8), ((96, 160, 96), 32)]
+
+
+def batch_metrics(precond: str = "amg", keep: dict | None = None):
     """The batching workload: channel 256x192x192 (m = 16), 64^3 (m = 4), 128^3 (m = 8) and
     96x160x96 (m = 32) in ONE ens_solve_batch launch, FP32 inner / FP64 refinement to 1e-10.
-    RHS-solves/s of the batch (set-up of the preconditioner excluded), per-system iterations and
-    the solution error of each system against its FP64 block solve to 1e-12."""
+    RHS-solves/s of the batch (set-up of the preconditioner excluded) against the one-RHS-at-a-time
+    solver on the same systems (every column solved alone, same preconditioner and precision, one
+    after the other), per-system iterations; the solutions are kept in `keep` for the error against
+    the oracle's references."""
     import numpy as np
     import torch
 
     import gen
     import paper_1711_10622_gb300 as ens
 
-    specs = [((256, 192, 192), 16), ((64, 64, 64), 4), ((128, 128, 128), 8), ((96, 160, 96), 32)]
+    keep = {} if keep is None else keep
     mats, Bs = [], []
     try:
-        for i, (dims, m) in enumerate(specs):
+        for i, (dims, m) in enumerate(BATCH_SPECS):
             op = gen.channel(*dims)
             A = ens.Matrix.from_operator(op)
             if precond == "amg":
@@ -328,18 +469,42 @@ def batch_metrics(precond: str = "amg"):
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         systems = []
-        for (dims, m), A, B, (X, st) in zip(specs, mats, Bs, res):
-            Xr, _ = ens.solve_block(A, B, tol=1e-12, precond=precond)
-            err = (torch.linalg.vector_norm(X - Xr, dim=0) / torch.linalg.vector_norm(Xr, dim=0)).max().item()
-            systems.append({"grid": "x".join(map(str, dims)), "m": m, "converged": int((st["status"] == 0).sum()),
+        for (dims, m), A, B, (X, st) in zip(BATCH_SPECS, mats, Bs, res):
+            g = "x".join(map(str, dims))
+            keep[g] = X.cpu().numpy()
+            systems.append({"grid": g, "m": m, "converged": int((st["status"] == 0).sum()),
                             "max_relres": float(np.max(st["relres"])), "iters_max": int(np.max(st["iters"])),
-                            "outer_max": int(np.max(st["outer"])), "max_rel_err_vs_fp64": err})
+                            "outer_max": int(np.max(st["outer"]))})
+        # one right-hand side at a time: every column of every system alone, one after the other
+        for A, B in zip(mats, Bs):  # warm the m = 1 code paths
+            ens.solve_block(A, B[:, :1].contiguous(), tol=1e-10, precond=precond, precision="mixed")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for A, B in zip(mats, Bs):
+            for l in range(B.shape[1]):
+                ens.solve_block(A, B[:, l : l + 1].contiguous(), tol=1e-10, precond=precond, precision="mixed")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter() - t1
     finally:
         for A in mats:
             A.close()
-    rhs = sum(m for _, m in specs)
+    rhs = sum(m for _, m in BATCH_SPECS)
     return {"precond": precond, "precision": "mixed", "tol": 1e-10, "rhs": rhs, "seconds": t, "rhs_solves_per_s": rhs / t,
-            "systems": systems}
+            "one_rhs": {"seconds": t1, "rhs_solves_per_s": rhs / t1, "how": "ens_solve_block with m = 1 per column, same systems, precond and precision"},
+            "speedup_vs_one_rhs": t1 / t, "systems": systems}
+
+
+def attach_batch_errors(batch: dict, keep: dict, refs: dict, sol_bar: float = 1e-6):
+    for sysd in batch["systems"]:
+        ref = refs.get(sysd["grid"])
+        if ref is None:
+            sysd["max_rel_err_vs_oracle"] = None
+            sysd["oracle_columns"] = "not compared: the oracle needs minutes on the host for one column of this system"
+            continue
+        err = rel_err_cols(keep[sysd["grid"]], ref["X"], ref["cols"])
+        sysd["max_rel_err_vs_oracle"] = err
+        sysd["meets_1e-6"] = err <= sol_bar
+        sysd["oracle_columns"] = ref["cols"]
 
 
 def fp64_peak_ops(sm_mhz=None):
@@ -399,38 +564,78 @@ def projection_metrics(m: int = 8, reps: int = 20):
     }
 
 
-def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = 5, budget: float = 120e9, slots: int = 4):
+SERVING_SEED = 5
+
+
+def serving_plan(ops, count: int, seed: int = SERVING_SEED):
+    """The serving stream's requests in arrival order: (operator name, m, first column of the block
+    taken from that operator's 64-column right-hand-side pool). Request k is the same whatever the
+    count (both draws are sequential)."""
+    import numpy as np
+
+    import gen
+
+    reqs = gen.serving_requests(count, ops, seed)
+    rng = np.random.default_rng(seed + 2)
+    return [(name, m, int(rng.integers(0, 64 - m + 1))) for name, m, _ in reqs]
+
+
+def serving_pool(ops, name: str):
+    """64 zero-mean N(0, 1) right-hand sides for one serving operator (seed by operator)."""
+    import gen
+
+    k = sorted(ops).index(name)
+    return gen.rhs_normal(ops[name].n, 64, 10622 + 500 + k, zero_mean=True)
+
+
+def serving_samples(ops, scan: int = 200, count: int = 4):
+    """Requests whose result is compared with the oracle: the first `count` of the stream on the 64^3
+    operators with m <= 4 (request index -> (operator, B))."""
+    import numpy as np
+
+    out = {}
+    for k, (name, m, c0) in enumerate(serving_plan(ops, scan)):
+        if name.endswith("64") and m <= 4:
+            out[k] = (name, np.ascontiguousarray(serving_pool(ops, name)[:, c0 : c0 + m]))
+            if len(out) == count:
+                break
+    return out
+
+
+def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budget: float = 120e9, slots: int = 4,
+                    keep: dict | None = None):
     """Poisson streams of solve requests (grids 64^3..192^3, channel and cube operators, m drawn from
     {1, 2, 4, 8, 16, 32}, FP32 inner + FP64 refinement to 1e-8, AMG-lite preconditioner) through the
     continuous-batching server under an HBM budget. The arrival rate of each stream is `load` times
     the capacity measured by a saturated burst of the same requests (one stream per load, the same
     requests and arrival seed). Latency = arrival to result on the host. The first load's summary is
-    the top level; every load's summary is under "loads"."""
+    the top level; every load's summary is under "loads". The results of the sampled requests
+    (serving_samples) of the first load are kept for the error against the oracle."""
     import gen
     from paper_1711_10622_gb300.serving import Request, Server, latency_summary
 
+    keep = {} if keep is None else keep
     ops = gen.serving_operators()
-    reqs = gen.serving_requests(count, ops, seed)
-    # one 64-column RHS pool per operator; a request takes m consecutive columns from a seeded offset
-    pools = {name: gen.rhs_normal(op.n, 64, 10622 + 500 + k, zero_mean=True) for k, (name, op) in enumerate(sorted(ops.items()))}
-    rng = __import__("numpy").random.default_rng(seed + 2)
+    plan = serving_plan(ops, count, seed)
+    pools = {name: serving_pool(ops, name) for name in sorted(ops)}
+    samples = set(serving_samples(ops))
 
-    def make(name, m):
-        c0 = int(rng.integers(0, 64 - m + 1))
+    def make(k):
+        name, m, c0 = plan[k]
         return Request(name, pools[name][:, c0 : c0 + m].copy(), 1e-8)
 
     out = []
     with Server(ops, budget_bytes=budget, slots=slots, max_cols=32, precond="amg") as srv:
         burst_n = min(16, count)
-        burst = [srv.submit(make(n, m)) for n, m, _ in reqs[:burst_n]]
+        burst = [srv.submit(make(k)) for k in range(burst_n)]
         for r in burst:
             r.done.wait(600)
         span = max(r.end for r in burst) - min(r.arrival for r in burst)
         cap_rps = burst_n / span
-        for load in loads:
+        for li, load in enumerate(loads):
             rate = load * cap_rps
             arrivals = gen.poisson_arrivals(count, rate, seed)
-            pending = [make(n, m) for n, m, _ in reqs]
+            pending = [make(k) for k in range(count)]
             srv.sched.peak_in_flight = 0
             t0 = time.perf_counter()
             for r, ta in zip(pending, arrivals):
@@ -440,6 +645,10 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = 5, budget: float =
                 srv.submit(r)
             for r in pending:
                 r.done.wait(900)
+            if li == 0:
+                for k in samples:
+                    if k < count and pending[k].done.is_set() and pending[k].X is not None:
+                        keep[k] = pending[k].X
             peak = srv.sched.peak_in_flight + srv.sched.resident
             unfinished = sum(1 for r in pending if not r.done.is_set())
             pending = [r for r in pending if r.done.is_set()]
@@ -462,29 +671,42 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = 5, budget: float =
             )
             out.append(s)
     top = dict(out[0])
-    top["loads"] = {str(s["load_vs_measured_capacity"]): {k: s[k] for k in ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "rhs_solves_per_s", "arrival_rate_per_s", "peak_admitted_gb", "errors", "converged_all", "unfinished") if k in s} for s in out}
+    top["loads"] = {str(s["load_vs_measured_capacity"]): {k: s[k] for k in ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "rhs_solves_per_s", "arrival_rate_per_s", "peak_admitted_gb", "errors", "converged_all", "unfinished", "mean_batch_requests") if k in s} for s in out}
     return top
 
 
+def attach_serving_errors(serving: dict, keep: dict, refs: dict, sol_bar: float = 1e-6):
+    errs = {}
+    for k, X in keep.items():
+        ref = refs.get(k)
+        if ref is None:
+            continue
+        errs[str(k)] = {"op": ref["op"], "m": int(X.shape[1]), "max_rel_err_vs_oracle": rel_err_cols(X, ref["X"], list(range(X.shape[1])))}
+    serving["oracle_samples"] = errs
+    serving["max_rel_err_vs_oracle"] = max((e["max_rel_err_vs_oracle"] for e in errs.values()), default=None)
+    if serving["max_rel_err_vs_oracle"] is not None:
+        serving["meets_1e-6"] = serving["max_rel_err_vs_oracle"] <= sol_bar
+
+
 def run_reference(args):
-    """The CPU oracle as it stands, on a bounded row sample of the same workload."""
+    """The CPU oracle as it stands, on the host cores, on the same workload as the GPU arm: each step
+    is one FP64 GSpMV per m on the full channel operator. The OpenMP build of the oracle source
+    (rows split over all host cores, the columns of a row together as in Fig. GSpMV; the same bits
+    as the serial oracle) when the compiler has OpenMP, else the serial build column by column."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import numpy as np
-
     import gen
     import oracle
 
     op = gen.channel(256, 128, 128)
-    rows = np.arange(0, op.n // 128)  # 32,768 contiguous rows (one x-y plane)
-    view = oracle.rows_view(op, rows)
-    sub_nnz = int(view[0][-1])
     Xs = {m: gen.rhs_normal(op.n, m, 20000 + m) for m in M_SWEEP}
+    par = oracle.lib_omp() is not None
+    fn = (lambda X: oracle.gspmv_rowwise(op, X, parallel=True)) if par else (lambda X: oracle.gspmv(op, X))
 
     def step():
         for m in M_SWEEP:
-            oracle.gspmv_csr(view, Xs[m])
+            fn(Xs[m])
 
     for _ in range(args.warmup):
         step()
@@ -492,9 +714,12 @@ def run_reference(args):
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    bytes_step = sum(alg_bytes(len(rows), sub_nnz, m) for m in M_SWEEP)
+    bytes_step = sum(alg_bytes(op.n, op.nnz, m) for m in M_SWEEP)
     value = bytes_step * args.steps / dt / 1e9
-    sample = f"rows 0..{len(rows) - 1} ({len(rows)} of {op.n}) of the {WORKLOAD} operator, one FP64 GSpMV per m in {list(M_SWEEP)} per step"
+    threads = oracle.threads(par)
+    how = (f"OpenMP build of the C oracle on {threads} threads, rows split, the columns of a row together" if par
+           else "serial C oracle on 1 core, column by column")
+    sample = f"the full {WORKLOAD} operator, one FP64 GSpMV per m in {list(M_SWEEP)} per step ({how})"
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -509,8 +734,9 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} GSpMV sweep m={list(M_SWEEP)} (row sample)", "rows": len(rows), "nnz": sub_nnz},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": f"{WORKLOAD} GSpMV sweep m={list(M_SWEEP)}", "n": op.n, "nnz": op.nnz},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -688,6 +914,8 @@ def main():
     ap.add_argument("--profile-modes", default="split,native,f32")
     ap.add_argument("--profile-share", type=int, default=-1, help="native-DFMA share (32nds) for split mode")
     ap.add_argument("--sweep", action="store_true", help="float64 arithmetic sweep (uses --profile-size/--profile-m)")
+    ap.add_argument("--oracle-refs", default="default", choices=["default", "full", "none"],
+                    help="oracle solutions for the error of every solve (full: also the 9.4M-row batch system)")
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)
@@ -697,6 +925,17 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+
+    # The oracle's reference solutions (for the error of every solve result) are computed on the host
+    # cores in a spawned process while the GPU sections run; started before the first GPU call.
+    refs_future, refs_pool = None, None
+    rank0 = int(os.environ.get("RANK", "0")) == 0
+    if rank0 and not args.no_solves and args.oracle_refs != "none":
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        refs_pool = cf.ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context("spawn"))
+        refs_future = refs_pool.submit(oracle_references, args.oracle_refs)
 
     import numpy as np
     import torch
@@ -818,10 +1057,11 @@ def main():
         "api": "ens_gspmv_host (pinned host X/Y)",
     }
 
-    solves = None if args.no_solves else solve_metrics()
+    keep_solves, keep_batch, keep_serving = {}, {}, {}
+    solves = None if args.no_solves else solve_metrics(keep=keep_solves)
     projection = None if args.no_solves else projection_metrics()
     cubes = None if args.no_solves else cubes_gspmv_metrics()
-    batch = None if args.no_solves else batch_metrics()
+    batch = None if args.no_solves else batch_metrics(keep=keep_batch)
     if cubes is not None:
         for v in cubes["sweep"].values():
             v["frac_of_measured_peak"] = v["gbs"] / peak
@@ -831,10 +1071,24 @@ def main():
             projection[k]["fp64_frac"] = projection[k]["fp64_gops"] / ceiling
             projection[k]["hbm_frac"] = projection[k]["gbs"] / peak
         projection["fp64_ceiling_gops"] = ceiling
-    serving = None if args.serving_requests <= 0 else serving_metrics(args.serving_requests)
+    serving = None if args.serving_requests <= 0 else serving_metrics(args.serving_requests, keep=keep_serving)
     from paper_1711_10622_gb300 import report
 
     estimate = report.estimate_table(per_m_us, n, nnz)
+
+    oracle_refs = None
+    if refs_future is not None:
+        t_wait = time.perf_counter()
+        refs = refs_future.result()
+        refs_pool.shutdown()
+        oracle_refs = {"host_seconds": refs["seconds"], "threads": refs["threads"],
+                       "waited_s": time.perf_counter() - t_wait, "level": args.oracle_refs}
+        if solves is not None:
+            attach_oracle_errors(solves, keep_solves, refs)
+        if batch is not None:
+            attach_batch_errors(batch, keep_batch, refs["batch"])
+        if serving is not None:
+            attach_serving_errors(serving, keep_serving, refs["serving"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -872,6 +1126,7 @@ def main():
             "serving": serving,
             "paper_estimate": estimate,
             "cpu_baseline": cpu,
+            "oracle_references": oracle_refs,
             "clocks": clocks,
             "gpu_launches": K * len(M_SWEEP),
         }

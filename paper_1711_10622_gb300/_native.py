@@ -148,6 +148,11 @@ def lib():
         "ens_amg_info": (_i32, [_vp, ctypes.POINTER(_i32), _vp, _vp]),
         "ens_amg_level": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp]),
         "ens_amg_apply": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+        "ens_create_matrix_rect": (_i32, [_i64, _i64, _i64, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+        "ens_matrix_shape": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+        "ens_block_dots": (_i32, [_i64, _i32, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]),
+        "ens_block_lincomb": (_i32, [_i64, _i32, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]),
+        "ens_gather_rows": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp]),
         "ens_last_error": (ctypes.c_char_p, []),
         "ens_version": (ctypes.c_char_p, []),
     }

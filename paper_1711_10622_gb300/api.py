@@ -327,6 +327,109 @@ def solve_batch(systems, stream=None, **opts):
     return out
 
 
+class RectMatrix(Matrix):
+    """A row block of a distributed matrix (ens_create_matrix_rect): n_rows rows whose columns index an
+    extended local vector of n_cols rows. Works with gspmv_rect."""
+
+    def __init__(self, row_ptr, col_idx, val, n_cols: int, stream=None):
+        L = N.lib()
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        h = ctypes.c_void_p()
+        N.check(
+            L.ens_create_matrix_rect(
+                row_ptr.shape[0] - 1,
+                int(n_cols),
+                col_idx.shape[0],
+                row_ptr.ctypes.data_as(ctypes.c_void_p),
+                col_idx.ctypes.data_as(ctypes.c_void_p),
+                val.ctypes.data_as(ctypes.c_void_p),
+                _stream_handle(stream),
+                ctypes.byref(h),
+            )
+        )
+        self._h = h
+        self.singular = False
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        N.check(L.ens_matrix_shape(self._h, ctypes.byref(r), ctypes.byref(c)))
+        self.n, self.n_cols = r.value, c.value
+        n_, nnz_, mr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        N.check(L.ens_matrix_info(self._h, ctypes.byref(n_), ctypes.byref(nnz_), ctypes.byref(mr)))
+        self.nnz, self.max_row_len = nnz_.value, mr.value
+
+
+def gspmv_rect(A: RectMatrix, X, Y, stream=None):
+    """Y (n_rows x m) = A X (n_cols x m) for a row block (ens_gspmv); float64 or float32 CUDA tensors."""
+    if not (X.is_cuda and Y.is_cuda and X.is_contiguous() and Y.is_contiguous()):
+        raise ValueError("X and Y must be contiguous CUDA tensors")
+    if X.shape[0] != A.n_cols or Y.shape[0] != A.n or X.shape[1] != Y.shape[1] or X.dtype != Y.dtype:
+        raise ValueError(f"shapes: X must be ({A.n_cols}, m) and Y ({A.n}, m) of one dtype")
+    N.check(
+        N.lib().ens_gspmv(A.handle, X.shape[1], _dtype_code(X), ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), _stream_handle(stream))
+    )
+    return Y
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = None if t is None else t.data_ptr()
+    return arr
+
+
+def _block_check(t, rows, m):
+    import torch
+
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.shape[0] < rows or t.shape[1] != m:
+        raise ValueError(f"blocks must be contiguous float64 CUDA tensors with >= {rows} rows and {m} columns")
+
+
+def block_dots(pairs, rows: int, out=None, stream=None):
+    """Per-column partial dots of the first `rows` rows of each pair (ens_block_dots):
+    out[k*m + l] = sum_i X_k[i, l] Y_k[i, l]; pairs = [(X_0, Y_0), ...] (at most 4)."""
+    import torch
+
+    m = pairs[0][0].shape[1]
+    for x, y in pairs:
+        _block_check(x, rows, m)
+        _block_check(y, rows, m)
+    if out is None:
+        out = torch.empty(len(pairs) * m, dtype=torch.float64, device=pairs[0][0].device)
+    xs, ys = _ptr_array([p[0] for p in pairs]), _ptr_array([p[1] for p in pairs])
+    N.check(N.lib().ens_block_dots(int(rows), m, len(pairs), xs, ys, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
+
+
+def block_lincomb(coefs, vecs, out, rows: int, stream=None):
+    """out[:rows] = sum_k diag(c_k) V_k[:rows] (ens_block_lincomb); c_k: float64 CUDA tensors of m
+    values or None (= 1). out may be one of the V_k."""
+    m = out.shape[1]
+    _block_check(out, rows, m)
+    for v in vecs:
+        _block_check(v, rows, m)
+    for c in coefs:
+        if c is not None and (c.numel() != m or not c.is_cuda or not c.is_contiguous()):
+            raise ValueError("coefficients must be contiguous CUDA tensors of m values")
+    N.check(
+        N.lib().ens_block_lincomb(int(rows), m, len(vecs), _ptr_array(coefs), _ptr_array(vecs), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+    )
+    return out
+
+
+def gather_rows(idx, X, out, stream=None):
+    """out[k] = X[idx[k]] row by row (ens_gather_rows); idx an int32 CUDA tensor."""
+    import torch
+
+    if idx.dtype != torch.int32 or not idx.is_cuda:
+        raise ValueError("idx must be an int32 CUDA tensor")
+    m = X.shape[1]
+    _block_check(X, 0, m)
+    _block_check(out, idx.numel(), m)
+    N.check(N.lib().ens_gather_rows(idx.numel(), m, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
+
+
 def version() -> str:
     return N.lib().ens_version().decode()
 

@@ -177,6 +177,7 @@ extern "C" ens_status ens_amg_setup(ens_matrix *A, const ens_amg_opts *opts, voi
 
 static ens_status amg_setup_impl(ens_matrix *A, const ens_amg_opts *opts, void *stream) {
   if (!A) return fail(ENS_ERR_INVALID, "amg_setup: matrix is NULL");
+  if (A->ncols != A->n) return fail(ENS_ERR_INVALID, "amg_setup: needs a square matrix");
   ens_amg_opts o;
   ens_default_amg_opts(&o);
   if (opts) o = *opts;

@@ -98,9 +98,9 @@ ens_status check_gspmv_args(const ens_matrix *A, int32_t m, int32_t dtype, const
   if (A->n > 0 && (!X || !Y)) return fail(ENS_ERR_INVALID, "gspmv: X or Y is NULL");
   const size_t es = dtype == ENS_F64 ? 8 : 4;
   if ((uintptr_t)X % es || (uintptr_t)Y % es) return fail(ENS_ERR_INVALID, "gspmv: X/Y not aligned to the element size");
-  const size_t bytes = (size_t)A->n * m * es;
+  const size_t xbytes = (size_t)A->ncols * m * es, ybytes = (size_t)A->n * m * es;
   const char *x = (const char *)X, *y = (const char *)Y;
-  if (A->n > 0 && x < y + bytes && y < x + bytes) return fail(ENS_ERR_INVALID, "gspmv: X and Y overlap");
+  if (A->n > 0 && x < y + ybytes && y < x + xbytes) return fail(ENS_ERR_INVALID, "gspmv: X and Y overlap");
   return ENS_OK;
 }
 
@@ -118,9 +118,20 @@ const char *ens_version(void) { return "ensemble_solve 0.1 (sm_103a)"; }
 ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                              const double *val, uint32_t flags, void *stream, ens_matrix **out) {
   clear_error();
+  return create_matrix(n, n, nnz, row_ptr, col_idx, val, flags, stream, out);
+}
+
+}  // extern "C"
+
+ens_status ens::create_matrix(int64_t n, int64_t ncols, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                              const double *val, uint32_t flags, void *stream, ens_matrix **out) {
   if (!out) return fail(ENS_ERR_INVALID, "create_matrix: out is NULL");
   *out = nullptr;
   if (n < 1 || n > INT32_MAX) return fail(ENS_ERR_INVALID, "create_matrix: n = %lld outside [1, 2^31-1]", (long long)n);
+  if (ncols < 1 || ncols > INT32_MAX)
+    return fail(ENS_ERR_INVALID, "create_matrix: ncols = %lld outside [1, 2^31-1]", (long long)ncols);
+  if (ncols != n && (flags & ENS_MATRIX_SINGULAR))
+    return fail(ENS_ERR_INVALID, "create_matrix: ENS_MATRIX_SINGULAR needs a square matrix");
   if (nnz < 0 || nnz > INT32_MAX) return fail(ENS_ERR_INVALID, "create_matrix: nnz = %lld outside [0, 2^31-1]", (long long)nnz);
   if (!row_ptr || (nnz > 0 && (!col_idx || !val))) return fail(ENS_ERR_INVALID, "create_matrix: NULL array");
   if (flags & ~ENS_MATRIX_SINGULAR) return fail(ENS_ERR_INVALID, "create_matrix: unknown flags 0x%x", flags);
@@ -134,12 +145,14 @@ ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, con
   }
   if (row_ptr[n] != nnz) return fail(ENS_ERR_INVALID, "create_matrix: row_ptr[n] = %d != nnz = %lld", row_ptr[n], (long long)nnz);
   for (int64_t j = 0; j < nnz; ++j)
-    if (col_idx[j] < 0 || col_idx[j] >= n)
-      return fail(ENS_ERR_INVALID, "create_matrix: col_idx[%lld] = %d outside [0, n)", (long long)j, col_idx[j]);
+    if (col_idx[j] < 0 || col_idx[j] >= ncols)
+      return fail(ENS_ERR_INVALID, "create_matrix: col_idx[%lld] = %d outside [0, %lld)", (long long)j, col_idx[j],
+                  (long long)ncols);
 
   cudaStream_t s = (cudaStream_t)stream;
   ens_matrix *A = new ens_matrix();
   A->n = n;
+  A->ncols = ncols;
   A->nnz = nnz;
   A->max_row_len = max_len;
   A->flags = flags;
@@ -198,6 +211,8 @@ ens_status ens_create_matrix(int64_t n, int64_t nnz, const int32_t *row_ptr, con
   return ENS_OK;
 }
 
+extern "C" {
+
 ens_status ens_destroy_matrix(ens_matrix *A) {
   clear_error();
   if (!A) return ENS_OK;
@@ -251,6 +266,7 @@ ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *
 ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream) {
   clear_error();
   if (!A) return fail(ENS_ERR_INVALID, "gspmv_host: matrix is NULL");
+  if (A->ncols != A->n) return fail(ENS_ERR_INVALID, "gspmv_host: needs a square matrix");
   if (m < 1) return fail(ENS_ERR_INVALID, "gspmv_host: m must be >= 1 (got %d)", m);
   if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "gspmv_host: unknown dtype %d", dtype);
   if (!X || !Y) return fail(ENS_ERR_INVALID, "gspmv_host: X or Y is NULL");

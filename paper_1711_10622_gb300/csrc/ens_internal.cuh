@@ -16,6 +16,8 @@ constexpr int kShareHybrid = 64;  // "native share" code of the column-hybrid FP
 
 struct ens_matrix {
   int64_t n = 0, nnz = 0;
+  int64_t ncols = 0;          // columns (= n for the square matrices of the solver; a row block of a
+                              // distributed matrix indexes an extended vector of ncols rows)
   int32_t max_row_len = 0;
   uint32_t flags = 0;
   int device = 0;
@@ -74,6 +76,10 @@ namespace ens {
 
 // Release a hierarchy (coarse matrices and maps; not the fine matrix).
 void free_amg(ens_amg *H);
+
+// Create a device matrix of n rows whose column indices lie in [0, ncols) (ncols = n: square).
+ens_status create_matrix(int64_t n, int64_t ncols, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                         const double *val, uint32_t flags, void *stream, ens_matrix **out);
 
 // Record a formatted message for ens_last_error() and return `st`.
 ens_status fail(ens_status st, const char *fmt, ...);

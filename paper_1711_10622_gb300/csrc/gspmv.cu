@@ -267,14 +267,14 @@ ens_status launch_gspmv_rows(const ens_matrix *A, int m, int dtype, const void *
 // matrix's table.
 ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *lanes_out, int32_t *share_out,
                     double *best_us_out) {
-  const size_t count = (size_t)A->n * m;
+  const size_t count = (size_t)A->n * m, xcount = (size_t)A->ncols * m;  // Y rows, X rows (= n if square)
   void *X = nullptr, *Y = nullptr;
   const size_t es = dtype == ENS_F32 ? 4 : 8;
-  cudaError_t e = cudaMallocAsync(&X, count * es, s);
+  cudaError_t e = cudaMallocAsync(&X, xcount * es, s);
   if (e == cudaSuccess) e = cudaMallocAsync(&Y, count * es, s);
   if (e == cudaSuccess) {
     const int grid = A->num_sms * 8;
-    k_tune_fill<<<grid, 256, 0, s>>>((int64_t)count, dtype == ENS_F32 ? nullptr : (double *)X,
+    k_tune_fill<<<grid, 256, 0, s>>>((int64_t)xcount, dtype == ENS_F32 ? nullptr : (double *)X,
                                      dtype == ENS_F32 ? (float *)X : nullptr);
     e = cudaGetLastError();
   }

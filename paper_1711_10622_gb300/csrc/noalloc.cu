@@ -34,6 +34,7 @@ extern "C" ens_status ens_gspmv_host_noalloc(const ens_matrix *A, int32_t m, int
                                              void *stream) {
   clear_error();
   if (!A) return fail(ENS_ERR_INVALID, "gspmv_host_noalloc: matrix is NULL");
+  if (A->ncols != A->n) return fail(ENS_ERR_INVALID, "gspmv_host_noalloc: needs a square matrix");
   if (m < 1) return fail(ENS_ERR_INVALID, "gspmv_host_noalloc: m must be >= 1 (got %d)", m);
   if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "gspmv_host_noalloc: unknown dtype %d", dtype);
   if (!X || !Y) return fail(ENS_ERR_INVALID, "gspmv_host_noalloc: X or Y is NULL");

@@ -41,6 +41,7 @@ namespace {
 ens_status validate_solve(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
                           const ens_solve_opts &o) {
   if (!A) return fail(ENS_ERR_INVALID, "solve_block: matrix is NULL");
+  if (A->ncols != A->n) return fail(ENS_ERR_INVALID, "solve_block: needs a square matrix");
   if (m < 1 || m > kMaxSolveM) return fail(ENS_ERR_INVALID, "solve_block: m = %d outside [1, %d]", m, kMaxSolveM);
   if (!B || !X) return fail(ENS_ERR_INVALID, "solve_block: B or X is NULL");
   if (!tol) return fail(ENS_ERR_INVALID, "solve_block: tol is NULL");
@@ -242,6 +243,7 @@ ens_status amg_apply_impl(const ens_matrix *A, int32_t m, const void *R, void *Z
 extern "C" ens_status ens_amg_apply(const ens_matrix *A, int32_t m, int32_t dtype, const void *R, void *Z, void *stream) {
   clear_error();
   if (!A || !A->amg) return fail(ENS_ERR_INVALID, "amg_apply: matrix has no hierarchy (ens_amg_setup)");
+  if (A->ncols != A->n) return fail(ENS_ERR_INVALID, "amg_apply: needs a square matrix");
   if (m < 1 || m > kMaxSolveM) return fail(ENS_ERR_INVALID, "amg_apply: m = %d outside [1, %d]", m, kMaxSolveM);
   if (!R || !Z) return fail(ENS_ERR_INVALID, "amg_apply: R or Z is NULL");
   if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "amg_apply: unknown dtype %d", dtype);
