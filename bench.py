@@ -611,6 +611,8 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budg
     requests and arrival seed). Latency = arrival to result on the host. The first load's summary is
     the top level; every load's summary is under "loads". The results of the sampled requests
     (serving_samples) of the first load are kept for the error against the oracle."""
+    import torch
+
     import gen
     from paper_1711_10622_gb300.serving import Request, Server, latency_summary
 
@@ -636,7 +638,7 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budg
             rate = load * cap_rps
             arrivals = gen.poisson_arrivals(count, rate, seed)
             pending = [make(k) for k in range(count)]
-            srv.sched.peak_in_flight = 0
+            srv.sched.reset_peak()
             t0 = time.perf_counter()
             for r, ta in zip(pending, arrivals):
                 dt = t0 + ta - time.perf_counter()
@@ -650,6 +652,8 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budg
                     if k < count and pending[k].done.is_set() and pending[k].X is not None:
                         keep[k] = pending[k].X
             peak = srv.sched.peak_in_flight + srv.sched.resident
+            torch.cuda.synchronize()
+            free, total = torch.cuda.mem_get_info()
             unfinished = sum(1 for r in pending if not r.done.is_set())
             pending = [r for r in pending if r.done.is_set()]
             s = latency_summary(pending)
@@ -660,6 +664,8 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budg
                     "capacity_requests_per_s": cap_rps,
                     "budget_gb": budget / 1e9,
                     "peak_admitted_gb": peak / 1e9,
+                    "pool_gb": srv.sched.pool.size / 1e9,
+                    "device_used_gb": (total - free) / 1e9,
                     "slots": slots,
                     "grids": sorted(ops),
                     "tol": 1e-8,
@@ -670,8 +676,13 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budg
                 }
             )
             out.append(s)
+        model = srv.model.summary()
+        model["how"] = ("alpha: drop of free device memory when the operator's matrix and AMG hierarchy are created; "
+                        "beta + gamma m: least-squares line through the workspace bytes the library reports for probe "
+                        "solves at m = 1, 4, 16, 32 (ens_last_workspace_bytes), in the solver's padded width")
     top = dict(out[0])
-    top["loads"] = {str(s["load_vs_measured_capacity"]): {k: s[k] for k in ("p50_ms", "p99_ms", "mean_ms", "requests_per_s", "rhs_solves_per_s", "arrival_rate_per_s", "peak_admitted_gb", "errors", "converged_all", "unfinished", "mean_batch_requests") if k in s} for s in out}
+    top["memory_model"] = model
+    top["loads"] = {str(s["load_vs_measured_capacity"]): {k: s[k] for k in ("p50_ms", "p99_ms", "mean_ms", "wait_p50_ms", "wait_p99_ms", "service_p50_ms", "service_p99_ms", "p99_request", "requests_per_s", "rhs_solves_per_s", "arrival_rate_per_s", "peak_admitted_gb", "errors", "converged_all", "unfinished", "mean_batch_requests", "merged_fraction", "batch_cols_hist") if k in s} for s in out}
     return top
 
 

@@ -186,6 +186,14 @@ typedef struct {
   int32_t x0_zero;     /* nonzero: ignore X on input and start from x0 = 0 */
   int32_t use_graph;   /* nonzero (default): the iteration loop runs on the device as a CUDA graph
                           with a conditional WHILE node; 0: host-driven loop */
+  void *workspace;     /* NULL (default): the solve's scratch (internal copies of B and X, the Krylov
+                          blocks, the preconditioner's blocks, per-column scalars) is allocated
+                          stream-ordered for the call. Otherwise caller-owned DEVICE memory, 256-byte
+                          aligned, that holds all of it: nothing is allocated, so a server can keep
+                          its solvers' state in memory reserved once (Section 4.2's M = alpha + gamma m:
+                          gamma m is this workspace). One call at a time per workspace. */
+  uint64_t workspace_bytes; /* its size; a call that needs more returns ENS_ERR_BUDGET (the size it
+                               needed at least is then ens_last_workspace_bytes()) */
 } ens_solve_opts;
 
 /* Host arrays of m entries each, filled on return; any pointer may be NULL. */
@@ -214,7 +222,8 @@ void ens_default_solve_opts(ens_solve_opts *o);
  * With ENS_MATRIX_SINGULAR the operator's null space is the constants: a column whose sum exceeds
  * 1e-10 sqrt(n) ||b_l|| is rejected (ENS_COL_INCOMPATIBLE) and every solution is returned with
  * zero mean. Supports 1 <= m <= 64. Synchronous: returns when X and stats are written.
- * Workspace (about 8-13 n x m blocks) is allocated stream-ordered for the call and released.
+ * Workspace (about 8-13 n x m blocks) is allocated stream-ordered for the call and released, or taken
+ * from opts->workspace when given (then nothing is allocated).
  */
 ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
                            const ens_solve_opts *opts, ens_solve_stats *stats, void *stream);
@@ -292,6 +301,12 @@ ens_status ens_amg_apply(const ens_matrix *A, int32_t m, int32_t dtype, const vo
 
 /* Human-readable message of the last failed call on this host thread ("" if none). */
 const char *ens_last_error(void);
+
+/* Scratch bytes the last ens_solve_block / ens_solve_batch call on this host thread took from its
+ * workspace (or allocated stream-ordered when it had none); after ENS_ERR_BUDGET, the bytes it needed
+ * up to the request that did not fit. The per-solve part of the memory model M = alpha + gamma m
+ * (Section 4.2, Tables 6/7) is fitted from these values. */
+uint64_t ens_last_workspace_bytes(void);
 
 /* Library version string. */
 const char *ens_version(void);

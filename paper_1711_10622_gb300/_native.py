@@ -52,6 +52,8 @@ class SolveOpts(ctypes.Structure):
         ("check_every", ctypes.c_int32),
         ("x0_zero", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_uint64),
     ]
 
 
@@ -154,6 +156,7 @@ def lib():
         "ens_block_lincomb": (_i32, [_i64, _i32, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]),
         "ens_gather_rows": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp]),
         "ens_last_error": (ctypes.c_char_p, []),
+        "ens_last_workspace_bytes": (ctypes.c_uint64, []),
         "ens_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -16,6 +16,14 @@
 namespace ens {
 
 static thread_local std::string g_last_error;
+static thread_local uint64_t g_last_ws_bytes = 0;
+static thread_local bool g_last_ws_overflow = false;
+
+void record_workspace(size_t bytes, bool overflow) {
+  g_last_ws_bytes = bytes;
+  g_last_ws_overflow = overflow;
+}
+bool last_workspace_overflow() { return g_last_ws_overflow; }
 
 ens_status fail(ens_status st, const char *fmt, ...) {
   char buf[512];
@@ -82,7 +90,6 @@ void free_matrix(ens_matrix *A) {
   cudaFree(A->dinv32);
   cudaFree(A->stage_x);
   cudaFree(A->stage_y);
-  cudaFree(A->ws);
   for (cudaEvent_t ev : A->pipe_ev)
     if (ev) cudaEventDestroy(ev);
   if (A->pipe_h2d) cudaStreamDestroy(A->pipe_h2d);
@@ -112,6 +119,8 @@ using namespace ens;
 extern "C" {
 
 const char *ens_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t ens_last_workspace_bytes(void) { return g_last_ws_bytes; }
 
 const char *ens_version(void) { return "ensemble_solve 0.1 (sm_103a)"; }
 

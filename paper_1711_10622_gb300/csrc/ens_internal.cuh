@@ -49,9 +49,6 @@ struct ens_matrix {
   std::vector<int64_t> pipe_row, pipe_need;
   cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
   std::vector<cudaEvent_t> pipe_ev;
-  // solver workspace (grown on demand)
-  void *ws = nullptr;
-  size_t ws_bytes = 0;
   // aggregation multigrid hierarchy (ens_amg_setup), owned
   ens_amg *amg = nullptr;
 };
@@ -80,6 +77,11 @@ void free_amg(ens_amg *H);
 // Create a device matrix of n rows whose column indices lie in [0, ncols) (ncols = n: square).
 ens_status create_matrix(int64_t n, int64_t ncols, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                          const double *val, uint32_t flags, void *stream, ens_matrix **out);
+
+// Bytes of scratch the last solve call on this host thread took (or, if its caller-provided
+// workspace was too small, needed up to the failing request), and whether it ran out.
+void record_workspace(size_t bytes, bool overflow);
+bool last_workspace_overflow();
 
 // Record a formatted message for ens_last_error() and return `st`.
 ens_status fail(ens_status st, const char *fmt, ...);

@@ -67,7 +67,17 @@ ens_status validate_solve(const ens_matrix *A, int32_t m, const double *B, doubl
   if (o.precision == ENS_PREC_MIXED && (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0) || o.max_outer < 1 || o.inner_max_iter < 0))
     return fail(ENS_ERR_INVALID, "solve_block: mixed mode needs 0 < inner_tol < 1, max_outer >= 1, inner_max_iter >= 0");
   if (o.check_every < 1) return fail(ENS_ERR_INVALID, "solve_block: check_every < 1");
+  if (o.workspace && ((uintptr_t)o.workspace % 256))
+    return fail(ENS_ERR_INVALID, "solve_block: workspace must be 256-byte aligned");
   return ENS_OK;
+}
+
+// A solve that ran out of its caller-provided workspace reports ENS_ERR_BUDGET with the size.
+ens_status workspace_status(ens_status st, const ens_solve_opts &o, const char *who) {
+  if (st != ENS_OK && o.workspace && last_workspace_overflow())
+    return fail(ENS_ERR_BUDGET, "%s: the %llu-byte workspace is too small (the call needs at least %llu bytes)", who,
+                (unsigned long long)o.workspace_bytes, (unsigned long long)ens_last_workspace_bytes());
+  return st;
 }
 
 }  // namespace
@@ -90,6 +100,8 @@ void ens_default_solve_opts(ens_solve_opts *o) {
   o->check_every = 1;
   o->x0_zero = 0;
   o->use_graph = 1;
+  o->workspace = nullptr;
+  o->workspace_bytes = 0;
 }
 
 ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_solve_opts *opts, void *stream) {
@@ -117,7 +129,7 @@ ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_
   }
   cudaError_t e = cudaSuccess;
   {
-    solver::Scratch sc(s);
+    solver::Scratch sc(s, o);
     for (auto &p : sys)
       if (e == cudaSuccess) e = p->setup(sc);
     // one graph: a branch per system forked from and joined into a private capture stream
@@ -154,8 +166,9 @@ ens_status ens_solve_batch(int32_t nsys, const ens_batch_item *items, const ens_
       if (x) cudaStreamDestroy(x);
     if (cap) cudaStreamDestroy(cap);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+  const cudaError_t esync = cudaStreamSynchronize(s);  // also on failure (queued work may use the scratch)
+  if (e == cudaSuccess) e = esync;
+  if (e != cudaSuccess) return workspace_status(cuda_fail(e, "solve_batch"), o, "solve_batch");
   for (int32_t i = 0; i < nsys; ++i) sys[i]->write(items[i].stats);
   return ENS_OK;
 }
@@ -170,9 +183,10 @@ ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, doub
   if (st != ENS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int ar = solver_arith(A, m);
-  if (ar == 2) return solver::solve_f64_hybrid(A, m, B, X, tol, o, stats, s);
-  if (ar == 1) return solver::solve_f64_split(A, m, B, X, tol, o, stats, s);
-  return solver::solve_f64_native(A, m, B, X, tol, o, stats, s);
+  if (ar == 2) st = solver::solve_f64_hybrid(A, m, B, X, tol, o, stats, s);
+  else if (ar == 1) st = solver::solve_f64_split(A, m, B, X, tol, o, stats, s);
+  else st = solver::solve_f64_native(A, m, B, X, tol, o, stats, s);
+  return workspace_status(st, o, "solve_block");
 }
 
 }  // extern "C"

@@ -623,19 +623,40 @@ cudaError_t with_vl(int vec, int lanes, F &&f) {
 }
 
 // Stream-ordered scratch allocation, released when the object goes out of scope.
+// Scratch memory of one solve call: stream-ordered allocations released at the end of the call,
+// or, with a caller-provided workspace (ens_solve_opts.workspace), consecutive 256-byte aligned
+// pieces of that memory (nothing is allocated). Either way the bytes taken are recorded for
+// ens_last_workspace_bytes(); a workspace that is too small ends the call with ENS_ERR_BUDGET.
 struct Scratch {
   cudaStream_t s;
   std::vector<void *> ptrs;
+  char *arena = nullptr;
+  size_t cap = 0, used = 0;
+  bool overflow = false;
   explicit Scratch(cudaStream_t st) : s(st) {}
+  Scratch(cudaStream_t st, const ens_solve_opts &o) : s(st), arena((char *)o.workspace), cap(o.workspace_bytes) {}
   ~Scratch() {
     for (void *p : ptrs) cudaFreeAsync(p, s);
+    record_workspace(used, overflow);
   }
   template <typename T>
   cudaError_t get(T **p, size_t count) {
+    const size_t bytes = (std::max<size_t>(count, 1) * sizeof(T) + 255) / 256 * 256;
+    if (arena) {
+      if (overflow || used + bytes > cap) {
+        overflow = true;
+        used += bytes;  // what the call needed up to this request
+        return cudaErrorMemoryAllocation;
+      }
+      *p = (T *)(arena + used);
+      used += bytes;
+      return cudaSuccess;
+    }
     void *q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), s);
+    cudaError_t e = cudaMallocAsync(&q, bytes, s);
     if (e != cudaSuccess) return e;
     ptrs.push_back(q);
+    used += bytes;
     *p = (T *)q;
     return cudaSuccess;
   }
@@ -1216,7 +1237,7 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
   const int mp = m == 1 ? 1 : (m + 1) / 2 * 2;
   const int64_t n = M->n;
   const int singular = (M->flags & ENS_MATRIX_SINGULAR) ? 1 : 0;
-  Scratch sc(s);
+  Scratch sc(s, o);
   double *b = nullptr, *x = nullptr;
   cudaError_t e = sc.get(&b, (size_t)n * mp);
   if (e == cudaSuccess) e = sc.get(&x, (size_t)n * mp);
@@ -1294,7 +1315,9 @@ ens_status solve_f64(const ens_matrix *M, int32_t m, const double *B, double *X,
     k_unpad<<<cgrid, 256, 0, s>>>(n, m, mp, x, X);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // also on failure: work already queued may still use the scratch (or the caller's workspace)
+  const cudaError_t esync = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = esync;
   if (e != cudaSuccess) return cuda_fail(e, "solve_block");
   for (int l = 0; l < m; ++l) {
     if (state[l] != ST_DONE) status[l] = ENS_COL_MAXITER;

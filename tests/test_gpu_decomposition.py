@@ -178,7 +178,14 @@ def test_ensemble_split_on_emulated_ranks(ens):
             return X.cpu().numpy(), share
 
         out = run_ranks(2, rank_fn)
+    # every rank holds the whole solution; each column is solved to the tolerance by an independent
+    # recurrence (its rounding depends on the block width it ran in), so it matches the one-block
+    # solve to the solution-error bar, and the oracle confirms its residual
     Xf = Xfull.cpu().numpy()
+    Bh = B.cpu().numpy()
     for X, share in out:
         err = np.linalg.norm(X - Xf, axis=0) / np.linalg.norm(Xf, axis=0)
-        assert err.max() <= 1e-9, err
+        assert err.max() <= 1e-6, err
+        R = Bh - oracle.gspmv(op, X)
+        assert np.all(np.linalg.norm(R, axis=0) <= 1.05e-9 * np.linalg.norm(Bh, axis=0))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
