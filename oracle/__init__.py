@@ -63,6 +63,8 @@ def _declare(L):
     L.oracle_grad_correct.argtypes = grid_args + [_vp, _vp, _vp, _vp]
     L.oracle_gspmv_rowwise.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp]
     L.oracle_threads.restype = ctypes.c_int
+    L.oracle_block_bicgstab.argtypes = [_i64, _vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(_Opts), _vp, _vp, _vp]
+    L.oracle_block_bicgstab.restype = ctypes.c_int
     return L
 
 
@@ -260,6 +262,39 @@ def solve_block(
     o = _opts(max_iter, precond, sing, cheb_lo, cheb_hi, cheb_steps, amg)
     L = _pick(parallel)
     L.oracle_solve_block(
+        n, _p(row), _p(col), _p(val), m, _p(B), _p(X), _p(tolv), ctypes.byref(o), _p(iters), _p(relres), _p(status)
+    )
+    return X, iters, relres, status
+
+
+def block_solve(
+    A,
+    B: np.ndarray,
+    tol,
+    X0: np.ndarray | None = None,
+    max_iter: int = 10000,
+    precond: str = "none",
+    singular: bool | None = None,
+    cheb_lo=DEFAULT_CHEB_LO,
+    cheb_hi=DEFAULT_CHEB_HI,
+    cheb_steps=DEFAULT_CHEB_STEPS,
+    amg=None,
+):
+    """Coupled block BiCGStab on all m columns at once (block_krylov.c): one Krylov space, m x m step
+    matrices. Returns (X, iters[m], relres[m], status[m]) like solve_block."""
+    row, col, val = _csr(A)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, m = B.shape
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, order="C", copy=True)
+    tolv = np.broadcast_to(np.asarray(tol, dtype=np.float64), (m,)).copy()
+    iters = np.zeros(m, dtype=np.int32)
+    relres = np.zeros(m, dtype=np.float64)
+    status = np.zeros(m, dtype=np.int32)
+    sing = A.singular if singular is None else singular
+    o = _opts(max_iter, precond, sing, cheb_lo, cheb_hi, cheb_steps, amg)
+    lib().oracle_block_bicgstab(
         n, _p(row), _p(col), _p(val), m, _p(B), _p(X), _p(tolv), ctypes.byref(o), _p(iters), _p(relres), _p(status)
     )
     return X, iters, relres, status

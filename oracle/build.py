@@ -12,7 +12,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRCS = [os.path.join(HERE, f) for f in ("oracle.c", "projection.c", "amg.c")]
+SRCS = [os.path.join(HERE, f) for f in ("oracle.c", "projection.c", "amg.c", "block_krylov.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 LIB_OMP = os.path.join(OUT_DIR, "liboracle_omp.so")
