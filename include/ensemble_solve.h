@@ -228,6 +228,26 @@ void ens_default_solve_opts(ens_solve_opts *o);
 ens_status ens_solve_block(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
                            const ens_solve_opts *opts, ens_solve_stats *stats, void *stream);
 
+/*
+ * Coupled block-Krylov variant of ens_solve_block: block BiCGStab (Guennouni, Jbilou and Sadok
+ * 2003), standing in for the multiple right-hand-side extension of the paper's solver library that
+ * Section 3 names without describing. The m columns build ONE Krylov space: alpha and beta are
+ * m x m matrices (R~^T V)^-1 (R~^T R) and -(R~^T V)^-1 (R~^T T) with the shadow block R~ = R_0,
+ * solved by LU with partial pivoting on the host, and omega = <T, S>_F / <T, T>_F is one scalar per
+ * block; right preconditioning M^-1 (ENS_PRECOND_NONE, _CHEBYSHEV or _AMG) on every column.
+ * Arguments as ens_solve_block; float64 only (ENS_ERR_UNSUPPORTED for ENS_PREC_MIXED or a caller
+ * workspace), 1 <= m <= 32. The block stops when every column's recursive residual meets its tol
+ * (after a half or a full step) or after max_iter iterations; every column reports the block's
+ * iteration count; a column is CONVERGED when its recursive residual meets its tolerance at exit,
+ * else MAXITER. Columns with b = 0, non-finite data or an incompatible b (singular operators) leave
+ * before the first iteration, as in ens_solve_block. BREAKDOWN for every remaining column: a zero
+ * pivot in R~^T V (e.g. two equal right-hand sides), <T, T>_F = 0, omega = 0 or a non-finite step.
+ * Gram products and updates cost O(n m^2) float64 multiply-adds per iteration (the FP64 pipe).
+ * Synchronous.
+ */
+ens_status ens_solve_block_coupled(const ens_matrix *A, int32_t m, const double *B, double *X, const double *tol,
+                                   const ens_solve_opts *opts, ens_solve_stats *stats, void *stream);
+
 /* One system of a batched solve. */
 typedef struct {
   const ens_matrix *A;    /* its matrix */

@@ -7,7 +7,7 @@ solve (divergence right-hand sides, pressure-gradient correction). The computati
 library libensemble_solve.so (include/ensemble_solve.h); this package is its Python binding.
 """
 
-from .api import COL_STATUS, EnsError, Grid, Matrix, amg_apply, divergence, grad_correct, gspmv, gspmv_host, solve_batch, solve_block, solve_opts, version  # noqa: F401
+from .api import COL_STATUS, EnsError, Grid, Matrix, amg_apply, divergence, grad_correct, gspmv, gspmv_host, solve_batch, solve_block, solve_block_coupled, solve_opts, version  # noqa: F401
 
 __all__ = [
     "Matrix",
@@ -17,6 +17,7 @@ __all__ = [
     "gspmv_host",
     "solve_block",
     "solve_batch",
+    "solve_block_coupled",
     "solve_opts",
     "divergence",
     "amg_apply",

@@ -140,6 +140,10 @@ def lib():
             [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp],
         ),
         "ens_solve_batch": (_i32, [_i32, ctypes.POINTER(BatchItem), ctypes.POINTER(SolveOpts), _vp]),
+        "ens_solve_block_coupled": (
+            _i32,
+            [_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _vp],
+        ),
         "ens_create_grid": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
         "ens_destroy_grid": (_i32, [_vp]),
         "ens_grid_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),

@@ -276,6 +276,29 @@ def solve_block(A: Matrix, B, X=None, tol=1e-8, stream=None, **opts):
     return X, {"iters": iters, "relres": relres, "status": status, "outer": outer}
 
 
+def solve_block_coupled(A: Matrix, B, X=None, tol=1e-8, stream=None, **opts):
+    """Coupled block BiCGStab on all m columns (ens_solve_block_coupled): one Krylov space, m x m
+    step matrices. Arguments and result as solve_block; float64 only."""
+    import torch
+
+    _check_block(A, B, "B")
+    if B.dtype != torch.float64:
+        raise TypeError("B must be float64")
+    m = B.shape[1]
+    if X is None:
+        X = torch.zeros_like(B)
+        opts.setdefault("x0_zero", True)
+    _check_block(A, X, "X")
+    tolv = np.ascontiguousarray(np.broadcast_to(np.asarray(tol, dtype=np.float64), (m,)))
+    st, d = _stats_arrays(m)
+    o = solve_opts(**opts)
+    N.check(
+        N.lib().ens_solve_block_coupled(A.handle, m, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                        tolv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), ctypes.byref(st), _stream_handle(stream))
+    )
+    return X, d
+
+
 def _stats_arrays(m):
     iters = np.zeros(m, dtype=np.int32)
     relres = np.zeros(m, dtype=np.float64)
