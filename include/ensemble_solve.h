@@ -101,8 +101,8 @@ ens_status ens_set_native_share(ens_matrix *A, int32_t share);
 
 /*
  * Autotuner: time the GSpMV launch candidates for block width m (1..64) and dtype on this matrix
- * (lanes per row, i.e. rows per warp and column-tile width; for FP64 also native DFMA vs split-float
- * with native shares 0, 8, 12, 16, 24 of 32, and the column hybrid) and keep the fastest for later
+ * (lanes per row, i.e. rows per warp and column-tile width; tiled or untiled rows; for FP64 also native
+ * DFMA vs split-float with native shares 0, 8, 12, 16, 24 of 32, and the column hybrid) and keep the fastest for later
  * ens_gspmv calls and for the solver's products of that width. Uses temporary device blocks of
  * n x m (stream-ordered, freed before return). Synchronous. Optional outputs: chosen lanes, chosen
  * share (32 = native, 64 = column hybrid), and the best time per launch in microseconds. A share
@@ -110,6 +110,14 @@ ens_status ens_set_native_share(ens_matrix *A, int32_t share);
  */
 ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, int32_t *lanes, int32_t *share,
                         double *best_us);
+
+/*
+ * The launch the autotuner chose for width m and dtype (-1 in every output where it has not run):
+ * lanes per row, native share (as ens_autotune reports it) and untiled = 1 when the rows are read
+ * straight from global memory instead of through shared-memory row tiles (both forms are timed).
+ */
+ens_status ens_tuned_variant(const ens_matrix *A, int32_t m, int32_t dtype, int32_t *lanes, int32_t *share,
+                             int32_t *untiled);
 
 /*
  * Generalised SpMV Y = A X (Section 2.3, Fig. GSpMV): for every row i and column l,

@@ -132,6 +132,7 @@ def lib():
             [_vp, _i32, _i32, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)],
         ),
         "ens_gspmv": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
+        "ens_tuned_variant": (_i32, [_vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
         "ens_gspmv_host": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_gspmv_host_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "ens_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),

@@ -93,7 +93,10 @@ class Matrix:
         N.check(
             N.lib().ens_autotune(self.handle, int(m), code, _stream_handle(stream), ctypes.byref(lanes), ctypes.byref(share), ctypes.byref(us))
         )
-        return {"m": int(m), "dtype": dtype, "lanes": lanes.value, "share": share.value, "best_us": us.value}
+        ul = ctypes.c_int32()
+        N.check(N.lib().ens_tuned_variant(self.handle, int(m), code, None, None, ctypes.byref(ul)))
+        return {"m": int(m), "dtype": dtype, "lanes": lanes.value, "share": share.value, "untiled": bool(ul.value == 1),
+                "best_us": us.value}
 
     def amg_setup(self, stream=None, **opts):
         """Build the aggregation multigrid hierarchy (ens_amg_setup); keyword overrides of

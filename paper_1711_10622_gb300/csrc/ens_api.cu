@@ -265,6 +265,19 @@ ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, i
   return autotune(A, m, dtype, (cudaStream_t)stream, lanes, share, best_us);
 }
 
+ens_status ens_tuned_variant(const ens_matrix *A, int32_t m, int32_t dtype, int32_t *lanes, int32_t *share,
+                             int32_t *untiled) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "tuned_variant: matrix is NULL");
+  if (m < 1 || m > kTuneMaxM) return fail(ENS_ERR_INVALID, "tuned_variant: m = %d outside [1, %d]", m, kTuneMaxM);
+  if (dtype != ENS_F64 && dtype != ENS_F32) return fail(ENS_ERR_INVALID, "tuned_variant: unknown dtype %d", dtype);
+  const int di = dtype == ENS_F32 ? 1 : 0;
+  if (lanes) *lanes = A->tuned_lanes[di][m];
+  if (share) *share = dtype == ENS_F32 ? 0 : A->tuned_share[m];
+  if (untiled) *untiled = A->tuned_direct[di][m];
+  return ENS_OK;
+}
+
 ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *X, void *Y, void *stream) {
   clear_error();
   ens_status st = check_gspmv_args(A, m, dtype, X, Y);

@@ -36,8 +36,10 @@ struct ens_matrix {
   // autotuned launch choices by block width m (-1: none): lanes per row [0: FP64, 1: FP32], share
   int8_t tuned_lanes[2][kTuneMaxM + 1];
   int8_t tuned_share[kTuneMaxM + 1];
+  int8_t tuned_direct[2][kTuneMaxM + 1];  // 1: rows straight from global memory (no tile), 0: tiled
   ens_matrix() {
-    for (int i = 0; i <= kTuneMaxM; ++i) tuned_lanes[0][i] = tuned_lanes[1][i] = tuned_share[i] = -1;
+    for (int i = 0; i <= kTuneMaxM; ++i)
+      tuned_lanes[0][i] = tuned_lanes[1][i] = tuned_share[i] = tuned_direct[0][i] = tuned_direct[1][i] = -1;
   }
   // staging buffers of ens_gspmv_host (grown on demand)
   void *stage_x = nullptr, *stage_y = nullptr;

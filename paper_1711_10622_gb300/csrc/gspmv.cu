@@ -71,6 +71,24 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<Arith, VEC>::value)
   gspmv_body<Arith, VEC, LANES>(A, m, X, Y, native_mask);
 }
 
+// Untiled variant (direct_rows): an autotuner candidate beside the tiled kernels.
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads, MinBlocks<Arith, VEC>::value)
+    gspmv_kernel_direct(MatView A, int32_t m, const typename Arith::T *__restrict__ X,
+                        typename Arith::T *__restrict__ Y, uint32_t native_mask) {
+  using T = typename Arith::T;
+  direct_rows<Arith, VEC, LANES>(A, m, X, native_mask,
+                                 [&](int64_t i, int32_t c, const T (&y)[VEC]) { store_vec_cs<T, VEC>(Y + i * m + c, y); });
+}
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    gspmv_kernel_direct_free(MatView A, int32_t m, const typename Arith::T *__restrict__ X,
+                             typename Arith::T *__restrict__ Y, uint32_t native_mask) {
+  using T = typename Arith::T;
+  direct_rows<Arith, VEC, LANES>(A, m, X, native_mask,
+                                 [&](int64_t i, int32_t c, const T (&y)[VEC]) { store_vec_cs<T, VEC>(Y + i * m + c, y); });
+}
+
 // A contiguous range of rows [r0, r1) of the product (r0 a multiple of kTileRows, so the shifted
 // row-pointer array keeps its 16-byte alignment).
 struct Rows {
@@ -78,23 +96,32 @@ struct Rows {
 };
 static_assert(kPipeAlignRows % kTileRows == 0, "row chunks must be whole tiles");
 
-int grid_for(const ens_matrix *A, int64_t rows, const void *kernel) {
+int grid_for(const ens_matrix *A, int64_t rows, const void *kernel, int64_t rows_per_block = kTileRows) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  const int64_t need = (rows + kTileRows - 1) / kTileRows;
+  const int64_t need = (rows + rows_per_block - 1) / rows_per_block;
   const int64_t full = (int64_t)A->num_sms * per_sm;
   return (int)(need < full ? need : full);
 }
 
 template <typename Arith, int VEC, int LANES>
-cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, const Rows &rows, cudaStream_t s) {
+cudaError_t run(const ens_matrix *A, int m, const void *X, void *Y, uint32_t mask, const Rows &rows, cudaStream_t s,
+                bool direct) {
   using T = typename Arith::T;
   MatView v = view_of(A);
   v.n = (int32_t)(rows.r1 - rows.r0);
   v.rp = A->row + rows.r0;
   T *y = (T *)Y + rows.r0 * m;
-  if constexpr (std::is_same<Arith, ArithF64Split>::value || std::is_same<Arith, ArithF32>::value) {
+  constexpr bool capped = std::is_same<Arith, ArithF64Split>::value || std::is_same<Arith, ArithF32>::value;
+  if constexpr (!std::is_same<Arith, ArithF64Hybrid>::value) {
+    if (direct) {
+      auto k = capped ? gspmv_kernel_direct<Arith, VEC, LANES> : gspmv_kernel_direct_free<Arith, VEC, LANES>;
+      k<<<grid_for(A, v.n, (const void *)k, kThreads / LANES), kThreads, 0, s>>>(v, m, (const T *)X, y, mask);
+      return cudaGetLastError();
+    }
+  }
+  if constexpr (capped) {
     auto k = gspmv_kernel_capped<Arith, VEC, LANES>;
     k<<<grid_for(A, v.n, (const void *)k), kThreads, 0, s>>>(v, m, (const T *)X, y, mask);
   } else {
@@ -115,14 +142,14 @@ bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 // Dispatch on LANES, a power of two in [1, 32].
 template <typename Arith, int VEC>
 cudaError_t dispatch(const ens_matrix *A, int m, const void *X, void *Y, int lanes, uint32_t mask, const Rows &rows,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool direct = false) {
   switch (lanes) {
-    case 1: return run<Arith, VEC, 1>(A, m, X, Y, mask, rows, s);
-    case 2: return run<Arith, VEC, 2>(A, m, X, Y, mask, rows, s);
-    case 4: return run<Arith, VEC, 4>(A, m, X, Y, mask, rows, s);
-    case 8: return run<Arith, VEC, 8>(A, m, X, Y, mask, rows, s);
-    case 16: return run<Arith, VEC, 16>(A, m, X, Y, mask, rows, s);
-    default: return run<Arith, VEC, 32>(A, m, X, Y, mask, rows, s);
+    case 1: return run<Arith, VEC, 1>(A, m, X, Y, mask, rows, s, direct);
+    case 2: return run<Arith, VEC, 2>(A, m, X, Y, mask, rows, s, direct);
+    case 4: return run<Arith, VEC, 4>(A, m, X, Y, mask, rows, s, direct);
+    case 8: return run<Arith, VEC, 8>(A, m, X, Y, mask, rows, s, direct);
+    case 16: return run<Arith, VEC, 16>(A, m, X, Y, mask, rows, s, direct);
+    default: return run<Arith, VEC, 32>(A, m, X, Y, mask, rows, s, direct);
   }
 }
 
@@ -163,6 +190,7 @@ namespace {
 // 32 / lanes, column tile = VEC * lanes); share of native-DFMA sweeps (FP64 only).
 struct Cfg {
   int vec, lanes, share;
+  bool direct = false;  // untiled rows (direct_rows) instead of shared-memory tiles
 };
 
 // VEC and full-width lanes of a float64 launch with native share `share`: split-float products take
@@ -203,16 +231,18 @@ Cfg default_cfg(const ens_matrix *A, int m, int dtype, const void *X, const void
   if (m >= 1 && m <= kTuneMaxM) {
     const int tl = A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m];
     if (tl > 0 && tl <= c.lanes) c.lanes = tl;  // tuned for the same share, hence VEC (alignment permitting)
+    c.direct = A->tuned_direct[dtype == ENS_F32 ? 1 : 0][m] == 1 && c.share != kShareHybrid;
   }
   return c;
 }
 
 cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, void *Y, const Cfg &c, const Rows &rows,
                        cudaStream_t s) {
+  const bool d = c.direct;
   if (dtype == ENS_F32) {
-    if (c.vec == 4) return dispatch<ArithF32, 4>(A, m, X, Y, c.lanes, 0u, rows, s);
-    if (c.vec == 2) return dispatch<ArithF32, 2>(A, m, X, Y, c.lanes, 0u, rows, s);
-    return dispatch<ArithF32, 1>(A, m, X, Y, c.lanes, 0u, rows, s);
+    if (c.vec == 4) return dispatch<ArithF32, 4>(A, m, X, Y, c.lanes, 0u, rows, s, d);
+    if (c.vec == 2) return dispatch<ArithF32, 2>(A, m, X, Y, c.lanes, 0u, rows, s, d);
+    return dispatch<ArithF32, 1>(A, m, X, Y, c.lanes, 0u, rows, s, d);
   }
   if (c.share == kShareHybrid) {  // column hybrid needs two columns per lane
     return c.vec == 2 ? dispatch<ArithF64Hybrid, 2>(A, m, X, Y, c.lanes, 0u, rows, s)
@@ -220,12 +250,12 @@ cudaError_t launch_cfg(const ens_matrix *A, int m, int dtype, const void *X, voi
   }
   if (c.share < 32) {
     const uint32_t mask = share_mask(c.share);
-    if (c.vec == 4) return dispatch<ArithF64Split, 4>(A, m, X, Y, c.lanes, mask, rows, s);
-    return c.vec == 2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, c.lanes, mask, rows, s)
-                      : dispatch<ArithF64Split, 1>(A, m, X, Y, c.lanes, mask, rows, s);
+    if (c.vec == 4) return dispatch<ArithF64Split, 4>(A, m, X, Y, c.lanes, mask, rows, s, d);
+    return c.vec == 2 ? dispatch<ArithF64Split, 2>(A, m, X, Y, c.lanes, mask, rows, s, d)
+                      : dispatch<ArithF64Split, 1>(A, m, X, Y, c.lanes, mask, rows, s, d);
   }
-  return c.vec == 2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, c.lanes, 0u, rows, s)
-                    : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, rows, s);
+  return c.vec == 2 ? dispatch<ArithF64Native, 2>(A, m, X, Y, c.lanes, 0u, rows, s, d)
+                    : dispatch<ArithF64Native, 1>(A, m, X, Y, c.lanes, 0u, rows, s, d);
 }
 
 // Deterministic N(0,1)-like fill of the tuning block (values in the split range, no zeros).
@@ -279,13 +309,18 @@ ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *la
     e = cudaGetLastError();
   }
   // the defaults without any previous tuning
-  const int keep_lanes = A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m], keep_share = A->tuned_share[m];
-  A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m] = -1;
+  const int di = dtype == ENS_F32 ? 1 : 0;
+  const int keep_lanes = A->tuned_lanes[di][m], keep_share = A->tuned_share[m], keep_direct = A->tuned_direct[di][m];
+  A->tuned_lanes[di][m] = -1;
+  A->tuned_direct[di][m] = -1;
   if (dtype != ENS_F32) A->tuned_share[m] = -1;
   const Cfg base = default_cfg(A, m, dtype, X, Y);
   std::vector<Cfg> cand;
   auto add_widths = [&](int vec, int full, int share) {
-    for (int div = 1; div <= 4 && full / div >= 1; div *= 2) cand.push_back(Cfg{vec, full / div, share});
+    for (int div = 1; div <= 4 && full / div >= 1; div *= 2) {
+      cand.push_back(Cfg{vec, full / div, share, false});
+      if (share != kShareHybrid) cand.push_back(Cfg{vec, full / div, share, true});
+    }
   };
   if (dtype == ENS_F32) {
     add_widths(base.vec, base.lanes, 0);
@@ -324,11 +359,13 @@ ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *la
   if (Y) cudaFreeAsync(Y, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m] = keep_lanes;
+    A->tuned_lanes[di][m] = keep_lanes;
     A->tuned_share[m] = keep_share;
+    A->tuned_direct[di][m] = keep_direct;
     return cuda_fail(e, "autotune");
   }
-  A->tuned_lanes[dtype == ENS_F32 ? 1 : 0][m] = bestc.lanes;
+  A->tuned_lanes[di][m] = bestc.lanes;
+  A->tuned_direct[di][m] = bestc.direct ? 1 : 0;
   if (dtype != ENS_F32) A->tuned_share[m] = bestc.share;
   if (lanes_out) *lanes_out = bestc.lanes;
   if (share_out) *share_out = bestc.share;

@@ -821,4 +821,28 @@ __device__ __forceinline__ void tile_rows(const MatView &A, int32_t m, const typ
   }
 }
 
+// Rows straight from global memory, without a shared-memory tile and without block barriers: row
+// group g of the grid takes rows g, g + groups, g + 2 groups, ... (consecutive groups, consecutive
+// rows); the lanes of a group read the row's column indices and values through L1 at the same
+// addresses. The native-DFMA rows of the split arithmetic are spread by the row index as the
+// tiled kernel spreads its sweeps.
+template <typename Arith, int VEC, int LANES, typename Epi>
+__device__ __forceinline__ void direct_rows(const MatView &A, int32_t m, const typename Arith::T *__restrict__ X,
+                                            uint32_t native_mask, Epi &&epi) {
+  using T = typename Arith::T;
+  constexpr int G = 256 / LANES;
+  const int lane = threadIdx.x % LANES;
+  const int64_t groups = (int64_t)gridDim.x * G;
+  const uint32_t rot = (threadIdx.x >> 5) * 5u + blockIdx.x;
+  for (int64_t i = (int64_t)blockIdx.x * G + threadIdx.x / LANES; i < A.n; i += groups) {
+    const int32_t j0 = __ldg(A.rp + i), j1 = __ldg(A.rp + i + 1);
+    const bool nat = (native_mask >> (((uint32_t)i + rot) & 31u)) & 1u;
+    for (int32_t c = lane * VEC; c < m; c += LANES * VEC) {
+      T y[VEC];
+      Arith::template row_g<VEC>(A, 0, j0, j1, m, c, X, y, nat);
+      epi(i, c, y);
+    }
+  }
+}
+
 }  // namespace ens
