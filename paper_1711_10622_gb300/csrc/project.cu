@@ -12,6 +12,7 @@
 
 #include "ens_internal.cuh"
 #include "ensemble_project.h"
+#include "rowprod.cuh"
 
 struct ens_grid {
   int32_t N[3] = {0, 0, 0};
@@ -30,6 +31,7 @@ struct ens_grid {
   double *inv_dist[3] = {nullptr, nullptr, nullptr};  // [N_d + 1] per face position (see below)
   double *area[3] = {nullptr, nullptr, nullptr};      // face areas normal to d, indexed by the other two
                                                       // coordinates (lower one fastest)
+  bool split_area = false;  // every area lies in the split-float product range [2^-40, 2^60)
 };
 
 namespace ens {
@@ -153,6 +155,100 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int q = 0; q < VEC; ++q) acc[q] *= scale;
     stv<VEC>(D + (int64_t)r * m + c, acc);
+  }
+}
+
+// The same divergence with split-float products (the GSpMV's arithmetic, rowprod.cuh): the FP64 pipe
+// of GB300 is narrow, and the native form spends 7 FP64 operations per cell and state; here the six
+// face products and their sum run on the FP32 pipe as packed pairs of states (split_acc2: each area and
+// face value carried as hi + lo floats, the sum accumulated error-free), and each output costs one
+// FP64 addition (the widening of hi + lo) and the scale multiply. A state whose face values leave the
+// split range (zero among them) is recomputed with native DFMA. VEC = 2 or 4 states per thread.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads, 4)
+    k_divergence_split(GridView g, int32_t m, double scale, const double *__restrict__ U, const double *__restrict__ V,
+                       const double *__restrict__ W, double *__restrict__ D) {
+  constexpr int NP = VEC / 2;
+  constexpr uint64_t kSign2 = 0x8000000080000000ull;
+  const int32_t groups = m / VEC;
+  const int64_t total = (int64_t)g.n * groups;
+  const double *comp[3] = {U, V, W};
+  const uint64_t g23 = f2_pack(__uint_as_float(kSplitG), __uint_as_float(kSplitG));
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(t / groups);
+    const int32_t c = (int32_t)(t - (int64_t)r * groups) * VEC;
+    const int32_t cell = g.all_fluid ? r : g.cell_of_row[r];
+    const int32_t p[3] = {cell % g.N[0], (cell / g.N[0]) % g.N[1], cell / (g.N[0] * g.N[1])};
+    const uint32_t op = g.open[r];
+    const double ar[3] = {g.area[0][p[1] + (int64_t)g.N[1] * p[2]], g.area[1][p[0] + (int64_t)g.N[0] * p[2]],
+                          g.area[2][p[0] + (int64_t)g.N[0] * p[1]]};
+    uint64_t sh[NP], sl[NP];
+    uint32_t rng[VEC];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) sh[q] = sl[q] = 0ull;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) rng[q] = 0u;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float ah, al;
+      split_f64(ar[d], ah, al);
+      const SplitPair a = split_pair(make_float2(ah, al));
+      int32_t lo[3] = {p[0], p[1], p[2]}, hi[3] = {p[0], p[1], p[2]};
+      hi[d] = (g.bc[d] == ENS_BC_PERIODIC && p[d] + 1 == g.N[d]) ? 0 : p[d] + 1;
+      if (op & (2u << (2 * d))) {
+        double u[VEC];
+        ldv<VEC>(comp[d] + face_at(g, d, hi[0], hi[1], hi[2]) * m + c, u);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) split_acc2(a, u[2 * q], u[2 * q + 1], g23, sh[q], sl[q], rng[2 * q], rng[2 * q + 1]);
+      }
+      if (op & (1u << (2 * d))) {
+        double u[VEC];
+        ldv<VEC>(comp[d] + face_at(g, d, lo[0], lo[1], lo[2]) * m + c, u);
+        const SplitPair na{a.ah ^ kSign2, a.al ^ kSign2};  // -area, exactly
+#pragma unroll
+        for (int q = 0; q < NP; ++q) split_acc2(na, u[2 * q], u[2 * q + 1], g23, sh[q], sl[q], rng[2 * q], rng[2 * q + 1]);
+      }
+    }
+    double y[VEC];
+    bool all_ok = true, ok[VEC];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      float h0, h1, l0, l1;
+      f2_unpack(sh[q], h0, h1);
+      f2_unpack(sl[q], l0, l1);
+      ok[2 * q] = split_ok(rng[2 * q], h0, l0);
+      ok[2 * q + 1] = split_ok(rng[2 * q + 1], h1, l1);
+      y[2 * q] = split_to_double(h0, l0);
+      y[2 * q + 1] = split_to_double(h1, l1);
+      all_ok &= ok[2 * q] && ok[2 * q + 1];
+    }
+    if (!all_ok) {  // native products for the states the split form cannot carry
+      double acc[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[q] = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int32_t lo[3] = {p[0], p[1], p[2]}, hi[3] = {p[0], p[1], p[2]};
+        hi[d] = (g.bc[d] == ENS_BC_PERIODIC && p[d] + 1 == g.N[d]) ? 0 : p[d] + 1;
+        if (op & (2u << (2 * d))) {
+          double u[VEC];
+          ldv<VEC>(comp[d] + face_at(g, d, hi[0], hi[1], hi[2]) * m + c, u);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[q] = fma(ar[d], u[q], acc[q]);
+        }
+        if (op & (1u << (2 * d))) {
+          double u[VEC];
+          ldv<VEC>(comp[d] + face_at(g, d, lo[0], lo[1], lo[2]) * m + c, u);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[q] = fma(-ar[d], u[q], acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) y[q] = ok[q] ? y[q] : acc[q];
+    }
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) y[q] *= scale;
+    stv<VEC>(D + (int64_t)r * m + c, y);
   }
 }
 
@@ -353,7 +449,12 @@ static ens_status create_grid_impl(int32_t nx, int32_t ny, int32_t nz, const dou
       for (int32_t ja = 0; ja < N[a]; ++ja) area[d][ja + (size_t)N[a] * jb] = width[a][ja] * width[b][jb];
   }
 
+  bool split_area = true;
+  for (int d = 0; d < 3; ++d)
+    for (double a : area[d]) split_area = split_area && a >= 0x1p-40 && a < 0x1p60;
+
   ens_grid *G = new ens_grid();
+  G->split_area = split_area;
   for (int d = 0; d < 3; ++d) {
     G->N[d] = N[d];
     G->bc[d] = bc[d];
@@ -435,7 +536,12 @@ extern "C" ens_status ens_divergence(const ens_grid *G, int32_t m, double scale,
   const GridView g = view_of(G);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t work = (int64_t)G->n * (m / vec);
-  if (vec == 4)
+  // split-float products on the FP32 pipe for two or four states per thread (native for one)
+  if (vec == 4 && G->split_area)
+    k_divergence_split<4><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
+  else if (vec == 2 && G->split_area)
+    k_divergence_split<2><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
+  else if (vec == 4)
     k_divergence<4><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
   else if (vec == 2)
     k_divergence<2><<<grid_blocks(G, work), kThreads, 0, s>>>(g, m, scale, U, V, W, D);
