@@ -632,8 +632,10 @@ def serving_metrics(count: int, loads=(0.7, 1.0), seed: int = SERVING_SEED, budg
     samples = set(serving_samples(ops))
 
     def make(k):
+        # a view of the pool's columns (the server copies a batch's columns when it runs); only the
+        # sampled requests keep their solution on the host
         name, m, c0 = plan[k]
-        return Request(name, pools[name][:, c0 : c0 + m].copy(), 1e-8)
+        return Request(name, pools[name][:, c0 : c0 + m], 1e-8, keep_x=k in samples)
 
     out = []
     with Server(ops, budget_bytes=budget, slots=slots, max_cols=32, precond="amg") as srv:

@@ -53,6 +53,7 @@ class Request:
     batch_size: int = 0
     batch_cols: int = 0
     workspace_bytes: int = 0
+    keep_x: bool = True  # False: the solution is not kept on the host (stats only; long streams)
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -411,7 +412,7 @@ class Server:
             Xh = np.asarray(X)
         c = 0
         for r in batch:
-            r.X = Xh[:, c : c + r.m].copy()
+            r.X = Xh[:, c : c + r.m].copy() if r.keep_x else None
             r.stats = {k: np.asarray(v)[c : c + r.m].copy() for k, v in st.items()}
             c += r.m
 
