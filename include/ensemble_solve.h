@@ -112,6 +112,14 @@ ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, i
                         double *best_us);
 
 /*
+ * Row traversal of ens_gspmv / ens_gspmv_host on A: -1 (default) the autotuner's choice per width
+ * (tiled without tuning), 0 always shared-memory row tiles, 1 always untiled rows (read straight from
+ * global memory; the column hybrid arithmetic always uses tiles). Results stay within the accuracy
+ * bound either way. ENS_ERR_INVALID for other values.
+ */
+ens_status ens_set_untiled(ens_matrix *A, int32_t mode);
+
+/*
  * The launch the autotuner chose for width m and dtype (-1 in every output where it has not run):
  * lanes per row, native share (as ens_autotune reports it) and untiled = 1 when the rows are read
  * straight from global memory instead of through shared-memory row tiles (both forms are timed).

@@ -127,6 +127,7 @@ def lib():
         "ens_matrix_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
         "ens_set_f64_mode": (_i32, [_vp, _i32]),
         "ens_set_native_share": (_i32, [_vp, _i32]),
+        "ens_set_untiled": (_i32, [_vp, _i32]),
         "ens_autotune": (
             _i32,
             [_vp, _i32, _i32, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)],

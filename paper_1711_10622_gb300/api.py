@@ -86,6 +86,10 @@ class Matrix:
         """Split-float FP64: 32nds of row sweeps on native DFMA (-1: library table/autotuner)."""
         N.check(N.lib().ens_set_native_share(self.handle, int(share)))
 
+    def set_untiled(self, mode: int):
+        """GSpMV row traversal: -1 autotuner's choice, 0 shared-memory tiles, 1 untiled rows."""
+        N.check(N.lib().ens_set_untiled(self.handle, int(mode)))
+
     def autotune(self, m: int, dtype: str = "f64", stream=None) -> dict:
         """Time the GSpMV candidates for width m and keep the fastest (ens_autotune)."""
         lanes, share, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()

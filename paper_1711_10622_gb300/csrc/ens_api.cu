@@ -265,6 +265,14 @@ ens_status ens_autotune(ens_matrix *A, int32_t m, int32_t dtype, void *stream, i
   return autotune(A, m, dtype, (cudaStream_t)stream, lanes, share, best_us);
 }
 
+ens_status ens_set_untiled(ens_matrix *A, int32_t mode) {
+  clear_error();
+  if (!A) return fail(ENS_ERR_INVALID, "set_untiled: matrix is NULL");
+  if (mode < -1 || mode > 1) return fail(ENS_ERR_INVALID, "set_untiled: mode %d outside [-1, 1]", mode);
+  A->untiled = mode;
+  return ENS_OK;
+}
+
 ens_status ens_tuned_variant(const ens_matrix *A, int32_t m, int32_t dtype, int32_t *lanes, int32_t *share,
                              int32_t *untiled) {
   clear_error();

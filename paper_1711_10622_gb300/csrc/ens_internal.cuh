@@ -33,6 +33,7 @@ struct ens_matrix {
   bool full_diag = false;     // every row has a nonzero diagonal entry
   int32_t f64_mode = ENS_F64_AUTO;
   int32_t native_share = -1;  // 32nds of row sweeps on native DFMA in split mode (-1: built-in table)
+  int32_t untiled = -1;       // -1: the autotuner's choice; 0: always shared-memory tiles; 1: always untiled
   // autotuned launch choices by block width m (-1: none): lanes per row [0: FP64, 1: FP32], share
   int8_t tuned_lanes[2][kTuneMaxM + 1];
   int8_t tuned_share[kTuneMaxM + 1];

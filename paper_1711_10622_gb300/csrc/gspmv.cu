@@ -233,6 +233,7 @@ Cfg default_cfg(const ens_matrix *A, int m, int dtype, const void *X, const void
     if (tl > 0 && tl <= c.lanes) c.lanes = tl;  // tuned for the same share, hence VEC (alignment permitting)
     c.direct = A->tuned_direct[dtype == ENS_F32 ? 1 : 0][m] == 1 && c.share != kShareHybrid;
   }
+  if (A->untiled >= 0) c.direct = A->untiled == 1 && c.share != kShareHybrid;
   return c;
 }
 

@@ -115,6 +115,35 @@ def test_gspmv_parity(ens, name, m, mode):
             _check_f64(op, X, Y)
 
 
+@pytest.mark.parametrize("name", list(OPS))
+@pytest.mark.parametrize("m", M_VALUES)
+@pytest.mark.parametrize("mode", ["native", "split", "f32"])
+def test_gspmv_parity_untiled(ens, name, m, mode):
+    """The untiled row traversal (no shared-memory tile) on every operator shape, forced."""
+    op = _op(name)
+    X = gen.rhs_normal(op.n, m, 900 + m)
+    with ens.Matrix.from_operator(op) as A:
+        A.set_untiled(1)
+        if mode == "f32":
+            X32 = X.astype(np.float32)
+            Y = ens.gspmv(A, torch.from_numpy(X32).cuda()).cpu().numpy()
+            _check_f32(op, X32, Y)
+            return
+        A.set_f64_mode(mode)
+        Y = ens.gspmv(A, torch.from_numpy(X).cuda()).cpu().numpy()
+    _check_f64(op, X, Y)
+
+
+@pytest.mark.parametrize("untiled", [0, 1])
+def test_gspmv_host_pipelined_both_traversals(ens, untiled):
+    op = gen.cubes(48, 32, 24, size=4)
+    X = gen.rhs_normal(op.n, 8, 77)
+    with ens.Matrix.from_operator(op) as A:
+        A.set_untiled(untiled)
+        Y = ens.gspmv_host(A, X)
+    _check_f64(op, X, Y)
+
+
 def test_gspmv_deterministic_and_on_side_stream(ens):
     op = _op("cubes48x32x24")
     X = torch.from_numpy(gen.rhs_normal(op.n, 8, 5)).cuda()
