@@ -793,6 +793,22 @@ def run_profile(args):
     op = gen.channel(*dims)
     ms = [int(v) for v in args.profile_m.split(",")]
     modes = args.profile_modes.split(",")
+    if modes[0].startswith("coupled-"):  # K iterations of the coupled block solver, cubes m = 8
+        precond = modes[0][len("coupled-"):]
+        cop = gen.WORKLOADS["cubes192x128x96_m8"]["op"]()
+        A = ens.Matrix.from_operator(cop)
+        if precond == "amg":
+            A.amg_setup()
+        B = torch.from_numpy(gen.rhs_normal(cop.n, 8, 7, zero_mean=True)).cuda()
+        ens.solve_block_coupled(A, B, tol=1e-8, precond=precond, max_iter=2)  # warm
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled")
+        ens.solve_block_coupled(A, B, tol=1e-30, precond=precond, max_iter=args.steps)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        A.close()
+        print(json.dumps({"profile": "coupled", "precond": precond, "workload": "cubes192x128x96", "m": 8, "iterations": args.steps}))
+        return 0
     if modes[0].startswith("solve-"):  # a short block solve (cubes 192x128x96, m = 8) in the range
         # solve-amg | solve-chebyshev (FP64), or with "-mixed": one outer step of the mixed-precision
         # solve whose FP32 inner solve runs K iterations; host-driven loop
