@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "ensemble_dist.h"
+#include "partials.cuh"
 #include "solver_impl.cuh"
 
 namespace ens {
@@ -71,13 +72,69 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Pass 2: C[e] = sum over blocks in block order.
-__global__ void k_gram_final(int32_t nblocks, int32_t ne, const double *__restrict__ partials, double *__restrict__ C) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+// Per-column reductions over an n x m block (column statistics, sums, residual norms): f(e, v) gives
+// the NV values of flat element e; thread t owns column t % m (the grid stride is a multiple of m),
+// sums its elements in order, and the block adds its threads' sums per column in thread order.
+// partials[b][q * m + l]; the second pass is k_partials_final.
+template <int NV, typename F>
+__global__ void __launch_bounds__(256) k_colred(int64_t total, int32_t m, int64_t stride, F f, double *partials) {
+  __shared__ double sm[NV][256];
+  const int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  if (t < stride)
+    for (int64_t e = t; e < total; e += stride) {
+      double v[NV];
+      f(e, v);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[q] += v[q];
+    }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sm[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * 256;
+  for (int j = threadIdx.x; j < NV * m; j += 256) {
+    const int q = j / m, l = j % m;
+    const int first = (int)((l - base % m + m) % m);
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * ne + e];
-    C[e] = s;
+    for (int u = first; u < 256; u += m)
+      if (base + u < stride) s += sm[q][u];
+    partials[(int64_t)blockIdx.x * NV * m + j] = s;
   }
+}
+
+// ||b||^2, sum(b) and the count of non-finite entries of b (and of x0 when given), per column.
+struct StatsF {
+  const double *B, *X;
+  __device__ void operator()(int64_t e, double (&v)[3]) const {
+    const double b = B[e];
+    v[0] = b * b;
+    v[1] = b;
+    v[2] = (!isfinite(b) || (X && !isfinite(X[e]))) ? 1.0 : 0.0;
+  }
+};
+struct SumF {
+  const double *X;
+  __device__ void operator()(int64_t e, double (&v)[1]) const { v[0] = X[e]; }
+};
+struct ResidF {
+  const double *B, *AX;
+  __device__ void operator()(int64_t e, double (&v)[1]) const {
+    const double r = B[e] - AX[e];
+    v[0] = r * r;
+  }
+};
+
+// X[e] = zero[l] ? 0 : X[e] - shift[l] for column l = e % m (zero-b columns, zero-mean solutions).
+__global__ void k_fix_cols(int64_t total, int32_t m, int64_t stride, double *X, const double *__restrict__ shift,
+                           const int32_t *__restrict__ zero) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= stride) return;
+  const int l = (int)(t % m);
+  const double sh = shift[l];
+  const bool z = zero[l] != 0;
+  for (int64_t e = t; e < total; e += stride) X[e] = z ? 0.0 : X[e] - sh;
 }
 
 struct Terms {
@@ -192,7 +249,7 @@ struct Coupled {
     lanes = 1;
     while (lanes * vec < mp) lanes <<= 1;
     grid = M->num_sms * 8;
-    ggrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kGramRows - 1) / kGramRows, (int64_t)M->num_sms * 2));
+    ggrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kGramRows - 1) / kGramRows, (int64_t)M->num_sms * 8));
   }
 
   cudaError_t setup() {
@@ -233,7 +290,7 @@ struct Coupled {
   cudaError_t gram(const double *U, const double *W1, int q1, const double *W2, int q2, std::vector<double> &C) {
     const int q = q1 + q2, ne = k * q;
     k_gram<<<ggrid, 256, 0, s>>>(n, mp, k, U, W1, q1, W2, q2, partials);
-    k_gram_final<<<(ne + 255) / 256, 256, 0, s>>>(ggrid, ne, partials, dmat);
+    k_partials_final<<<partials_final_grid(ne), 256, 0, s>>>(ggrid, ne, partials, dmat);
     cudaError_t e = cudaGetLastError();
     C.assign(ne, 0.0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C.data(), dmat, ne * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -288,65 +345,74 @@ std::vector<double> scaled_identity(int k, double c) {
   return I;
 }
 
+// Per-column reduction of an n x m block through k_colred + k_partials_final; the NV * m results
+// ([q][l]) are read back to the host.
+template <int NV, typename F>
+cudaError_t column_reduce(int64_t n, int32_t m, F f, int grid, double *partials, double *dout, double *hout,
+                          cudaStream_t s) {
+  const int64_t stride = (int64_t)grid * 256 / m * m;
+  k_colred<NV><<<grid, 256, 0, s>>>(n * m, m, stride, f, partials);
+  k_partials_final<<<partials_final_grid(NV * m), 256, 0, s>>>(grid, NV * m, partials, dout);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hout, dout, (size_t)NV * m * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
 template <typename Arith>
 ens_status solve_coupled(const ens_matrix *M, int32_t m, const double *B, double *X, const double *tol,
                          const ens_solve_opts &o, ens_solve_stats *st, cudaStream_t s) {
   const int64_t n = M->n;
   const bool singular = (M->flags & ENS_MATRIX_SINGULAR) != 0;
-  // per-column start checks on the host (the columns are read back once)
-  std::vector<double> hb((size_t)n * m), hx((size_t)n * m);
-  ENS_CUDA_TRY(cudaMemcpyAsync(hb.data(), B, hb.size() * 8, cudaMemcpyDeviceToHost, s));
-  if (!o.x0_zero) ENS_CUDA_TRY(cudaMemcpyAsync(hx.data(), X, hx.size() * 8, cudaMemcpyDeviceToHost, s));
-  ENS_CUDA_TRY(cudaStreamSynchronize(s));
   std::vector<int32_t> status(m, ENS_COL_CONVERGED), iters(m, 0), idx;
   std::vector<double> relres(m, std::nan("")), bn(m, 0.0);
   std::vector<char> zero_b(m, 0);
-  for (int l = 0; l < m; ++l) {
-    double s2 = 0.0, sum = 0.0;
-    bool fin = true;
-    for (int64_t i = 0; i < n; ++i) {
-      const double b = hb[i * m + l];
-      s2 += b * b;
-      sum += b;
-      if (!std::isfinite(b) || (!o.x0_zero && !std::isfinite(hx[i * m + l]))) fin = false;
-    }
-    bn[l] = std::sqrt(s2);
-    if (!fin) status[l] = ENS_COL_NONFINITE;
-    else if (bn[l] == 0.0) {
-      zero_b[l] = 1;
-      relres[l] = 0.0;
-    } else if (singular && std::fabs(sum) > 1e-10 * std::sqrt((double)n) * bn[l]) status[l] = ENS_COL_INCOMPATIBLE;
-    else idx.push_back(l);
-  }
-  const int k = (int)idx.size();
   cudaError_t e = cudaSuccess;
+  ens_status gst = ENS_OK;
   int it = 0;
   {
     Scratch sc(s, o);
+    // per-column start checks on the device: ||b||^2, sum(b), non-finite entries of b and x0
+    const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>((n * m + 255) / 256, (int64_t)M->num_sms * 4));
+    double *rpart = nullptr, *rout = nullptr;
+    e = sc.get(&rpart, (size_t)rgrid * 3 * m);
+    if (e == cudaSuccess) e = sc.get(&rout, (size_t)3 * m);
+    std::vector<double> cs(3 * m, 0.0);
+    if (e == cudaSuccess)
+      e = column_reduce<3>(n, m, StatsF{B, o.x0_zero ? nullptr : X}, rgrid, rpart, rout, cs.data(), s);
+    if (e == cudaSuccess)
+      for (int l = 0; l < m; ++l) {
+        bn[l] = std::sqrt(cs[l]);
+        if (cs[2 * m + l] != 0.0) status[l] = ENS_COL_NONFINITE;
+        else if (bn[l] == 0.0) {
+          zero_b[l] = 1;
+          relres[l] = 0.0;
+        } else if (singular && std::fabs(cs[m + l]) > 1e-10 * std::sqrt((double)n) * bn[l])
+          status[l] = ENS_COL_INCOMPATIBLE;
+        else idx.push_back(l);
+      }
+    const int k = (int)idx.size();
     Coupled<Arith> C(M, m, std::max(k, 1), o, s, sc);
     const int mp = C.mp;
     const size_t blk = (size_t)n * mp;
     double *Xb, *Bb, *R, *Rt, *P, *Ph, *V, *S, *Sh, *T;
     int32_t *didx = nullptr;
     Xb = Bb = R = Rt = P = Ph = V = S = Sh = T = nullptr;
-    for (double **p : {&Xb, &Bb, &R, &Rt, &P, &Ph, &V, &S, &Sh, &T})
-      if (e == cudaSuccess) e = sc.get(p, blk);
-    if (e == cudaSuccess) e = sc.get(&didx, (size_t)std::max(k, 1));
-    // every block starts at zero, so the padding column (odd k) stays zero through every product
-    for (double *p : {Xb, Bb, R, Rt, P, Ph, V, S, Sh, T})
-      if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, blk * sizeof(double), s);
-    if (e == cudaSuccess) e = C.setup();
     const int cg = M->num_sms * 8;
     if (e == cudaSuccess && k > 0) {
-      e = cudaMemcpyAsync(didx, idx.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+      for (double **p : {&Xb, &Bb, &R, &Rt, &P, &Ph, &V, &S, &Sh, &T})
+        if (e == cudaSuccess) e = sc.get(p, blk);
+      if (e == cudaSuccess) e = sc.get(&didx, (size_t)k);
+      // every block starts at zero, so the padding column (odd k) stays zero through every product
+      for (double *p : {Xb, Bb, R, Rt, P, Ph, V, S, Sh, T})
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, blk * sizeof(double), s);
+      if (e == cudaSuccess) e = C.setup();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(didx, idx.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) {
         k_gather_cols<<<cg, 256, 0, s>>>(n, m, mp, k, didx, B, Bb);
-        if (o.x0_zero)
-          e = cudaMemsetAsync(Xb, 0, blk * sizeof(double), s);
-        else
-          k_gather_cols<<<cg, 256, 0, s>>>(n, m, mp, k, didx, X, Xb);
+        if (!o.x0_zero) k_gather_cols<<<cg, 256, 0, s>>>(n, m, mp, k, didx, X, Xb);
+        e = cudaGetLastError();
       }
-      if (e == cudaSuccess) e = cudaGetLastError();
       // R = B - A X, R~ = R, P = R
       if (e == cudaSuccess) e = C.spmv(Xb, R);
       std::vector<double> I1 = scaled_identity(k, -1.0);
@@ -445,48 +511,45 @@ ens_status solve_coupled(const ens_matrix *M, int32_t m, const double *B, double
         e = cudaGetLastError();
       }
     }
+    // zero right-hand sides: x = 0; singular operators: zero-mean solutions of the solved columns
+    bool any_zero = false;
+    for (int l = 0; l < m; ++l) any_zero = any_zero || zero_b[l];
+    if (e == cudaSuccess && (any_zero || (singular && k > 0))) {
+      std::vector<double> shift(m, 0.0);
+      if (singular && k > 0) {
+        std::vector<double> sums(m, 0.0);
+        e = column_reduce<1>(n, m, SumF{X}, rgrid, rpart, rout, sums.data(), s);
+        for (int l : idx) shift[l] = sums[l] / (double)n;
+      }
+      std::vector<int32_t> zf(m, 0);
+      for (int l = 0; l < m; ++l) zf[l] = zero_b[l];
+      double *dshift = nullptr;
+      int32_t *dzero = nullptr;
+      if (e == cudaSuccess) e = sc.get(&dshift, (size_t)m);
+      if (e == cudaSuccess) e = sc.get(&dzero, (size_t)m);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dshift, shift.data(), m * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dzero, zf.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) {
+        k_fix_cols<<<rgrid, 256, 0, s>>>(n * m, m, (int64_t)rgrid * 256 / m * m, X, dshift, dzero);
+        e = cudaGetLastError();
+      }
+    }
+    // true residuals ||b - A x|| / ||b|| of the solved columns
+    if (e == cudaSuccess && k > 0) {
+      double *AX = nullptr;
+      e = sc.get(&AX, (size_t)n * m);
+      if (e == cudaSuccess) gst = launch_gspmv(M, m, ENS_F64, X, AX, s);
+      if (gst != ENS_OK) e = cudaErrorLaunchFailure;
+      std::vector<double> r2(m, 0.0);
+      if (e == cudaSuccess) e = column_reduce<1>(n, m, ResidF{B, AX}, rgrid, rpart, rout, r2.data(), s);
+      if (e == cudaSuccess)
+        for (int l : idx) relres[l] = std::sqrt(r2[l]) / bn[l];
+    }
     const cudaError_t esync = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = esync;
   }
+  if (gst != ENS_OK) return gst;
   if (e != cudaSuccess) return cuda_fail(e, "solve_block_coupled");
-  // zero right-hand sides: x = 0; singular operators: zero-mean solutions; true residuals
-  {
-    ENS_CUDA_TRY(cudaMemcpyAsync(hx.data(), X, hx.size() * 8, cudaMemcpyDeviceToHost, s));
-    ENS_CUDA_TRY(cudaStreamSynchronize(s));
-    bool changed = false;
-    for (int l = 0; l < m; ++l) {
-      if (zero_b[l]) {
-        for (int64_t i = 0; i < n; ++i) hx[i * m + l] = 0.0;
-        changed = true;
-      }
-    }
-    if (singular)
-      for (int l : idx) {
-        double mean = 0.0;
-        for (int64_t i = 0; i < n; ++i) mean += hx[i * m + l];
-        mean /= (double)n;
-        for (int64_t i = 0; i < n; ++i) hx[i * m + l] -= mean;
-        changed = true;
-      }
-    if (changed) ENS_CUDA_TRY(cudaMemcpyAsync(X, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice, s));
-    double *AX = nullptr;
-    ENS_CUDA_TRY(cudaMallocAsync(&AX, hx.size() * 8, s));
-    const ens_status gs = launch_gspmv(M, m, ENS_F64, X, AX, s);
-    std::vector<double> hax(hx.size());
-    cudaError_t e2 = cudaMemcpyAsync(hax.data(), AX, hax.size() * 8, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(AX, s);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-    if (gs != ENS_OK) return gs;
-    if (e2 != cudaSuccess) return cuda_fail(e2, "solve_block_coupled residual");
-    for (int l : idx) {
-      double s2 = 0.0;
-      for (int64_t i = 0; i < n; ++i) {
-        const double r = hb[i * m + l] - hax[i * m + l];
-        s2 += r * r;
-      }
-      relres[l] = std::sqrt(s2) / bn[l];
-    }
-  }
   if (st) {
     for (int l = 0; l < m; ++l) {
       if (st->iters) st->iters[l] = iters[l];

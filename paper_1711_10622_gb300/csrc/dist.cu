@@ -10,6 +10,7 @@
 
 #include "ens_internal.cuh"
 #include "ensemble_dist.h"
+#include "partials.cuh"
 
 namespace ens {
 namespace {
@@ -60,15 +61,6 @@ __global__ void __launch_bounds__(kThreads)
     for (int u = first; u < kThreads; u += m)
       if (base + u < stride) s += sm[k][u];
     partials[(int64_t)blockIdx.x * npairs * m + j] = s;
-  }
-}
-
-// Pass 2: out[j] = sum over blocks in block order.
-__global__ void k_dots_final(int32_t nblocks, int32_t width, const double *__restrict__ partials, double *out) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < width; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * width + j];
-    out[j] = s;
   }
 }
 
@@ -149,7 +141,7 @@ ens_status ens_block_dots(int64_t n, int32_t m, int32_t npairs, const double *co
   k_dots_partial<<<grid, kThreads, 0, s>>>(total, m, npairs, px, py, stride, partials);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
-    k_dots_final<<<(npairs * m + 255) / 256, 256, 0, s>>>(grid, npairs * m, partials, out);
+    k_partials_final<<<partials_final_grid(npairs * m), 256, 0, s>>>(grid, npairs * m, partials, out);
     e = cudaGetLastError();
   }
   const cudaError_t ef = cudaFreeAsync(partials, s);
