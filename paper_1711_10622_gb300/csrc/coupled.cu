@@ -12,13 +12,15 @@
 // of the main solver on every column of the block, a block Gram kernel (U^T [W1 W2], fixed
 // summation order), a block update kernel (Y = Z0 + sum_t Z_t M_t with m x m matrices M_t) and the
 // per-column dots. The m x m factorisations run on the host (three small synchronisations per
-// iteration). Gram products and updates cost O(n m^2) float64 multiply-adds per iteration, which on
-// GB300's narrow FP64 pipe is the price of the coupling.
+// iteration). Gram products and updates cost O(n m^2) multiply-adds per iteration; on the split path
+// they run as split-float products on the FP32 pipe (GB300's FP64 pipe is narrow), otherwise as
+// native DFMA.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "ensemble_dist.h"
@@ -171,6 +173,265 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------- split-float block kernels
+// On the split path the Gram products and block updates run on the FP32 pipe like the GSpMV: each
+// double is cut into (hi, lo) floats (split_f64), products are formed as ah*bh (rounded) plus its
+// exact rounding error plus ah*bl + al*bh, and sums are carried as float pairs through TwoSum, two
+// columns per packed f32x2 instruction. Relative to sum |a||b| the error is about 2^-44 (the
+// truncation of x, the dropped al*bl, the float rounding of the low sums).
+//
+// An element takes the split form when it is zero or 2^-40 <= |x| < 2^44: then every nonzero
+// product of two such elements lies in [2^-80, 2^88), its error terms stay normal floats, and a sum
+// of up to 2^31 of them cannot overflow. A row (update) or tile (Gram) that holds any other value is
+// computed with native DFMA instead.
+__device__ __forceinline__ bool blk_split_ok(double x) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  return (((hw >> 20) & 0x7FFu) - 983u < 84u) || (((hw & 0x7FFFFFFFu) | lw) == 0u);
+}
+
+// (sh, sl) += (ah + al) * (bh + bl) on two packed float lanes.
+__device__ __forceinline__ void acc_pair(uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl, uint64_t &sh,
+                                         uint64_t &sl) {
+  const uint64_t ph = f2_mul(ah, bh);
+  uint64_t pl = f2_fma(ah, bh, ph ^ 0x8000000080000000ull);  // exact error of ah*bh (-ph by sign flip)
+  pl = f2_fma(ah, bl, pl);
+  pl = f2_fma(al, bh, pl);
+  const uint64_t t = f2_add(sh, ph);
+  const uint64_t bb = f2_sub(t, sh);
+  const uint64_t e = f2_add(f2_sub(sh, f2_sub(t, bb)), f2_sub(ph, bb));
+  sh = t;
+  sl = f2_add(sl, f2_add(e, pl));
+}
+
+__device__ __forceinline__ bool pair_finite(uint64_t v) {
+  float a, b;
+  f2_unpack(v, a, b);
+  return split_finite(a) && split_finite(b);
+}
+
+// (hi + lo) of lane c of a packed pair, widened exactly.
+__device__ __forceinline__ double pair_value(uint64_t sh, uint64_t sl, int c) {
+  float h0, h1, l0, l1;
+  f2_unpack(sh, h0, h1);
+  f2_unpack(sl, l0, l1);
+  return c == 0 ? widen_f32(h0) + widen_f32(l0) : widen_f32(h1) + widen_f32(l1);
+}
+
+struct SplitTerms {
+  const double *Z[3];
+  const float4 *Ms[3];  // [p][j], p < ld, j < ld / 2: {hi M[p][2j], hi M[p][2j+1], lo M[p][2j], lo M[p][2j+1]}
+  const double *Md[3];  // k x k row-major (the native fallback)
+};
+
+// Y[i, q] = Z0[i, q] + sum_t sum_p Z_t[i, p] M_t[p, q], ld even (ld = k or k + 1 with a zero padding
+// column; M_t is zero-padded to ld x ld, so the padding column keeps Z0's zero). A group of G lanes
+// owns one row, lane j the columns 2j and 2j + 1 (j < ld / 2): it splits its two Z_t values, and
+// every lane takes each pair in turn from its owner by shuffle. Each lane reads its own elements
+// before it writes them (Y may be Z0 or a Z_t).
+template <int G>
+__global__ void __launch_bounds__(256)
+    k_bupdate_split(int64_t n, int32_t ld, int32_t k, const double *Z0, SplitTerms tm, int32_t nt, double *Y) {
+  __shared__ float4 sm[3][kMaxCoupledM * kMaxCoupledM / 2];
+  const int half = ld / 2;
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+    if (t < nt)
+      for (int e = threadIdx.x; e < ld * half; e += blockDim.x) sm[t][e] = tm.Ms[t][e];
+  __syncthreads();
+  const int lane = threadIdx.x % G;
+  const bool own = lane < half;
+  const int lc = own ? lane : 0;
+  const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << ((threadIdx.x % 32) / G * G));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x / G) + threadIdx.x / G; i < n; i += groups) {
+    const int64_t off = i * ld + 2 * lc;
+    double2 y0 = make_double2(0.0, 0.0), z[3];
+    if (own) y0 = *reinterpret_cast<const double2 *>(Z0 + off);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      z[t] = make_double2(0.0, 0.0);
+      if (t < nt && own) z[t] = *reinterpret_cast<const double2 *>(tm.Z[t] + off);
+    }
+    uint64_t sh = 0, sl = 0;
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      if (t >= nt) break;
+      bad = bad || !blk_split_ok(z[t].x) || !blk_split_ok(z[t].y);
+      float h0, l0, h1, l1;
+      split_f64(z[t].x, h0, l0);
+      split_f64(z[t].y, h1, l1);
+      const float4 *M = sm[t];
+      for (int j = 0; j < half; ++j) {
+        const float a0 = __shfl_sync(gmask, h0, j, G), b0 = __shfl_sync(gmask, l0, j, G);
+        const float a1 = __shfl_sync(gmask, h1, j, G), b1 = __shfl_sync(gmask, l1, j, G);
+        const float4 m0 = M[(2 * j) * half + lc], m1 = M[(2 * j + 1) * half + lc];
+        acc_pair(f2_pack(a0, a0), f2_pack(b0, b0), f2_pack(m0.x, m0.y), f2_pack(m0.z, m0.w), sh, sl);
+        acc_pair(f2_pack(a1, a1), f2_pack(b1, b1), f2_pack(m1.x, m1.y), f2_pack(m1.z, m1.w), sh, sl);
+      }
+    }
+    bad = bad || !pair_finite(sh) || !pair_finite(sl);
+    double2 y;
+    if (__any_sync(gmask, bad)) {  // the whole group recomputes the row with native DFMA
+      y = y0;
+      const int q0 = 2 * lc, q1 = 2 * lc + 1;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        if (t >= nt) break;
+        for (int p = 0; p < k; ++p) {
+          const double zp = __shfl_sync(gmask, (p & 1) ? z[t].y : z[t].x, p >> 1, G);
+          if (own && q0 < k) y.x = fma(zp, __ldg(tm.Md[t] + p * k + q0), y.x);
+          if (own && q1 < k) y.y = fma(zp, __ldg(tm.Md[t] + p * k + q1), y.y);
+        }
+      }
+    } else {
+      y.x = y0.x + pair_value(sh, sl, 0);
+      y.y = y0.y + pair_value(sh, sl, 1);
+    }
+    if (own) *reinterpret_cast<double2 *>(Y + off) = y;
+  }
+}
+
+constexpr int kGramStage = 768;  // staged elements per tile (3 per thread)
+
+// Column jj of the padded Gram layout [W1 (ld) | W2 (ld)] as a column of C (-1: a padding column).
+__device__ __forceinline__ int gram_real_col(int jj, int ld, int q1, int q2) {
+  const int q1p = q1 > 0 ? ld : 0;
+  return jj < q1p ? (jj < q1 ? jj : -1) : (jj - q1p < q2 ? q1 + jj - q1p : -1);
+}
+
+// Pass 1 of C (k x q) = U^T [W1 | W2] on the split path.
+// Tiles of R rows (R even, R w <= 768 with w = ld + qp, qp = ld or 2 ld, ld even) of the row layout
+// [U (ld) | W1 (ld) | W2 (ld)] are staged as split (hi, lo) floats, transposed: column c, rows
+// (2 rp, 2 rp + 1) form one packed pair at c * RPs + rp (RPs odd, so consecutive columns fall in
+// different banks), and one 64-bit shared load gives a packed operand for two rows at once. Each
+// thread loads its three elements of the next tile into registers while the current one is
+// computed. Thread t owns the entries (i, j) and (i, j + qp / 2) for e = t % np (np = k qp / 2; i =
+// e / (qp / 2), j = e % (qp / 2); with np > 256, e = t, t + 256, ...), the two sharing the U loads,
+// and with np <= 128 the row pairs rp = s, s + S, ... of each tile (slice s = t / np, S = 256 / np).
+// The two packed lanes (even and odd rows) and then the slices are added in order at the end;
+// partials[b][i * q + j] for the real columns. A tile holding a value outside the split window is
+// computed with native DFMA.
+// EPT: entry pairs per thread the kernel is compiled for (1 when np <= 256, else 4).
+template <int EPT>
+__global__ void __launch_bounds__(256)
+    k_gram_split(int64_t n, int32_t ld, int32_t k, const double *__restrict__ U, const double *__restrict__ W1,
+                 int32_t q1, const double *__restrict__ W2, int32_t q2, double *__restrict__ partials) {
+  __shared__ uint64_t st_hi[kGramStage / 2 + 96], st_lo[kGramStage / 2 + 96];
+  __shared__ double red[512];
+  const int q1p = q1 > 0 ? ld : 0, qp = q1p + (q2 > 0 ? ld : 0), hp = qp / 2;
+  const int w = ld + qp, R = (kGramStage / w) & ~1, RPs = (R / 2) | 1;
+  const int np = k * hp;
+  const int S = np >= 256 ? 1 : 256 / np;
+  const int ept = np > 256 ? (np + 255) / 256 : 1;  // <= EPT (k <= 32, qp <= 64)
+  const int slice = np >= 256 ? 0 : (int)threadIdx.x / np;
+  const bool active = slice < S;
+  // this thread's three staged elements: source column pointer, tile row, float slot in the stage
+  const double *src[3];
+  int srow[3], sslot[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int v = (int)threadIdx.x + u * 256;
+    const int r = v / w, c = v % w;
+    srow[u] = v < R * w ? r : R;  // R: no element
+    src[u] = c < ld ? U + c : (c < ld + q1p ? W1 + (c - ld) : W2 + (c - ld - q1p));
+    sslot[u] = (c * RPs + r / 2) * 2 + (r & 1);
+  }
+  uint64_t ah[EPT], al[EPT], bh[EPT], bl[EPT];
+  double nat[EPT][2];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    ah[u] = al[u] = bh[u] = bl[u] = 0;
+    nat[u][0] = nat[u][1] = 0.0;
+  }
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(n, r0 + per);
+  double x[3];
+  auto fetch = [&](int64_t base) {
+    const int rows = (int)min((int64_t)R, r1 - base);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) x[u] = srow[u] < rows ? src[u][(base + srow[u]) * ld] : 0.0;
+  };
+  if (r0 < r1) fetch(r0);
+  float *fh = reinterpret_cast<float *>(st_hi), *fl = reinterpret_cast<float *>(st_lo);
+  for (int64_t base = r0; base < r1; base += R) {
+    const int rows = (int)min((int64_t)R, r1 - base);
+    __syncthreads();  // the previous tile's products are done with the stage
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (srow[u] < R) {  // rows past the end of the block's range are staged as zeros
+        bad = bad || !blk_split_ok(x[u]);
+        split_f64(x[u], fh[sslot[u]], fl[sslot[u]]);
+      }
+    const bool tile_bad = __syncthreads_or(bad) != 0;
+    if (base + R < r1) fetch(base + R);
+    if (!active) continue;
+    const int rps = (rows + 1) / 2;
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = (np >= 256 ? (int)threadIdx.x + u * 256 : (int)threadIdx.x % np);
+      if (u >= ept || e >= np) break;
+      const int i = e / hp, j = e % hp;
+      if (!tile_bad) {
+        const uint64_t *uh = st_hi + i * RPs, *ul = st_lo + i * RPs;
+        const uint64_t *wah = st_hi + (ld + j) * RPs, *wal = st_lo + (ld + j) * RPs;
+        const uint64_t *wbh = st_hi + (ld + j + hp) * RPs, *wbl = st_lo + (ld + j + hp) * RPs;
+        for (int rp = slice; rp < rps; rp += S) {
+          const uint64_t xh = uh[rp], xl = ul[rp];
+          acc_pair(xh, xl, wah[rp], wal[rp], ah[u], al[u]);
+          acc_pair(xh, xl, wbh[rp], wbl[rp], bh[u], bl[u]);
+        }
+      } else {
+        const int ja = j, jb = j + hp;
+        const double *Wa = ja < q1p ? W1 + ja : W2 + (ja - q1p);
+        const double *Wb = jb < q1p ? W1 + jb : W2 + (jb - q1p);
+        for (int rp = slice; rp < rps; rp += S)
+          for (int h = 0; h < 2; ++h) {
+            const int r = 2 * rp + h;
+            if (r >= rows) break;
+            const int64_t o = (base + r) * ld;
+            const double uv = U[o + i];
+            nat[u][0] = fma(uv, Wa[o], nat[u][0]);
+            nat[u][1] = fma(uv, Wb[o], nat[u][1]);
+          }
+      }
+    }
+  }
+  __syncthreads();
+  // per owned entry pair: even rows + odd rows + the native tiles; then the slices in order
+  const int q = q1 + q2;
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int e = (np >= 256 ? (int)threadIdx.x + u * 256 : (int)threadIdx.x % np);
+    if (u >= ept || !active || e >= np) break;
+    const double va = (pair_value(ah[u], al[u], 0) + pair_value(ah[u], al[u], 1)) + nat[u][0];
+    const double vb = (pair_value(bh[u], bl[u], 0) + pair_value(bh[u], bl[u], 1)) + nat[u][1];
+    if (S == 1) {
+      const int i = e / hp, j = e % hp;
+      const int ca = gram_real_col(j, ld, q1, q2), cb = gram_real_col(j + hp, ld, q1, q2);
+      if (ca >= 0) partials[(int64_t)blockIdx.x * k * q + i * q + ca] = va;
+      if (cb >= 0) partials[(int64_t)blockIdx.x * k * q + i * q + cb] = vb;
+    } else {
+      red[2 * threadIdx.x] = va;
+      red[2 * threadIdx.x + 1] = vb;
+    }
+  }
+  if (S == 1) return;
+  __syncthreads();
+  if ((int)threadIdx.x < np) {
+    const int e = threadIdx.x, i = e / hp, j = e % hp;
+    double va = 0.0, vb = 0.0;
+    for (int sidx = 0; sidx < S; ++sidx) {
+      va += red[2 * (sidx * np + e)];
+      vb += red[2 * (sidx * np + e) + 1];
+    }
+    const int ca = gram_real_col(j, ld, q1, q2), cb = gram_real_col(j + hp, ld, q1, q2);
+    if (ca >= 0) partials[(int64_t)blockIdx.x * k * q + i * q + ca] = va;
+    if (cb >= 0) partials[(int64_t)blockIdx.x * k * q + i * q + cb] = vb;
+  }
+}
+
 // ---------------------------------------------------------------- host helpers
 // Solve G Y = F (k x k, row-major) by LU with partial pivoting; false on a zero pivot or a
 // non-finite result. G is not modified.
@@ -240,7 +501,9 @@ struct Coupled {
   ens_amg single;  // one-level "hierarchy" = the Chebyshev polynomial preconditioner
   solver::AmgCycle<Arith> pre;
   bool use_pre = false;
-  double *partials = nullptr, *dmat = nullptr, *dots = nullptr;
+  double *partials = nullptr, *dmat = nullptr, *dots = nullptr, *mbuf = nullptr;
+  // split-float Gram products and block updates (the matrix runs on the split path)
+  static constexpr bool kSplit = std::is_same<Arith, ArithF64Split>::value;
 
   Coupled(const ens_matrix *M_, int m_, int k_, const ens_solve_opts &o_, cudaStream_t s_, Scratch &sc_)
       : M(M_), n(M_->n), m(m_), k(k_), o(o_), s(s_), sc(sc_) {
@@ -249,13 +512,30 @@ struct Coupled {
     lanes = 1;
     while (lanes * vec < mp) lanes <<= 1;
     grid = M->num_sms * 8;
-    ggrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kGramRows - 1) / kGramRows, (int64_t)M->num_sms * 8));
+    // one wave of the Gram kernel (its blocks each take a contiguous share of the rows)
+    int per_sm = 8;
+    if (kSplit && mp % 2 == 0) {
+      const cudaError_t oe =
+          gram_wide() ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_split<4>, 256, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_split<1>, 256, 0);
+      if (oe != cudaSuccess) {
+        (void)cudaGetLastError();  // not a launch error: fall back to one block per SM
+        per_sm = 1;
+      }
+      per_sm = std::max(per_sm, 1);
+    }
+    ggrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kGramRows - 1) / kGramRows, (int64_t)M->num_sms * per_sm));
   }
+
+  // the widest Gram of an iteration (q = 2k: np = k mp pair entries) needs four per thread
+  bool gram_wide() const { return k * mp > 256; }
 
   cudaError_t setup() {
     cudaError_t e = sc.get(&partials, (size_t)ggrid * kMaxCoupledM * 2 * kMaxCoupledM);
     if (e == cudaSuccess) e = sc.get(&dmat, (size_t)3 * kMaxCoupledM * kMaxCoupledM + 2 * kMaxCoupledM * kMaxCoupledM);
     if (e == cudaSuccess) e = sc.get(&dots, (size_t)4 * kMaxSolveM);
+    // update matrices: 3 k x k doubles, then 3 ld x ld / 2 float4 (two doubles each) split copies
+    if (e == cudaSuccess) e = sc.get(&mbuf, (size_t)6 * kMaxCoupledM * kMaxCoupledM);
     if (e != cudaSuccess) return e;
     if (o.precond == ENS_PRECOND_AMG) {
       use_pre = true;
@@ -289,7 +569,12 @@ struct Coupled {
   // host C (k x (q1 + q2)) = U^T [W1 W2]
   cudaError_t gram(const double *U, const double *W1, int q1, const double *W2, int q2, std::vector<double> &C) {
     const int q = q1 + q2, ne = k * q;
-    k_gram<<<ggrid, 256, 0, s>>>(n, mp, k, U, W1, q1, W2, q2, partials);
+    if (kSplit && mp % 2 == 0 && (q2 > 0 ? k * mp : k * mp / 2) > 256)
+      k_gram_split<4><<<ggrid, 256, 0, s>>>(n, mp, k, U, W1, q1, W2, q2, partials);
+    else if (kSplit && mp % 2 == 0)
+      k_gram_split<1><<<ggrid, 256, 0, s>>>(n, mp, k, U, W1, q1, W2, q2, partials);
+    else
+      k_gram<<<ggrid, 256, 0, s>>>(n, mp, k, U, W1, q1, W2, q2, partials);
     k_partials_final<<<partials_final_grid(ne), 256, 0, s>>>(ggrid, ne, partials, dmat);
     cudaError_t e = cudaGetLastError();
     C.assign(ne, 0.0);
@@ -315,16 +600,39 @@ struct Coupled {
   }
   // Y = Z0 + sum_t Z_t M_t (host matrices, k x k row-major)
   cudaError_t update(double *Y, const double *Z0, std::vector<std::pair<const double *, std::vector<double>>> terms) {
-    Terms tm{};
-    std::vector<double> hm;
-    for (auto &t : terms) hm.insert(hm.end(), t.second.begin(), t.second.end());
-    cudaError_t e = cudaMemcpyAsync(dmat, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-    for (size_t t = 0; t < terms.size(); ++t) {
-      tm.Z[t] = terms[t].first;
-      tm.M[t] = dmat + t * (size_t)k * k;
-    }
-    if (e != cudaSuccess) return e;
     const int nt = (int)terms.size();
+    std::vector<double> hm((size_t)6 * kMaxCoupledM * kMaxCoupledM, 0.0);
+    for (int t = 0; t < nt; ++t) std::copy(terms[t].second.begin(), terms[t].second.end(), hm.begin() + (size_t)t * k * k);
+    const size_t soff = (size_t)3 * kMaxCoupledM * kMaxCoupledM;  // start of the split copies
+    const bool split = kSplit && mp % 2 == 0 && split_matrices(terms, reinterpret_cast<float4 *>(hm.data() + soff));
+    const size_t bytes = split ? hm.size() * sizeof(double) : (size_t)nt * k * k * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(mbuf, hm.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (split) {
+      SplitTerms st{};
+      const size_t sz = (size_t)mp * (mp / 2);
+      for (int t = 0; t < nt; ++t) {
+        st.Z[t] = terms[t].first;
+        st.Md[t] = mbuf + (size_t)t * k * k;
+        st.Ms[t] = reinterpret_cast<const float4 *>(mbuf + soff) + t * sz;
+      }
+      const int half = mp / 2;
+      const int gsz = half <= 1 ? 1 : half <= 2 ? 2 : half <= 4 ? 4 : half <= 8 ? 8 : 16;
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n * gsz + 255) / 256, (int64_t)M->num_sms * 8));
+      switch (gsz) {
+        case 1: k_bupdate_split<1><<<blocks, 256, 0, s>>>(n, mp, k, Z0, st, nt, Y); break;
+        case 2: k_bupdate_split<2><<<blocks, 256, 0, s>>>(n, mp, k, Z0, st, nt, Y); break;
+        case 4: k_bupdate_split<4><<<blocks, 256, 0, s>>>(n, mp, k, Z0, st, nt, Y); break;
+        case 8: k_bupdate_split<8><<<blocks, 256, 0, s>>>(n, mp, k, Z0, st, nt, Y); break;
+        default: k_bupdate_split<16><<<blocks, 256, 0, s>>>(n, mp, k, Z0, st, nt, Y); break;
+      }
+      return cudaGetLastError();
+    }
+    Terms tm{};
+    for (int t = 0; t < nt; ++t) {
+      tm.Z[t] = terms[t].first;
+      tm.M[t] = mbuf + (size_t)t * k * k;
+    }
     const int gsz = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n * gsz + 255) / 256, (int64_t)M->num_sms * 8));
     switch (gsz) {
@@ -336,6 +644,28 @@ struct Coupled {
       default: k_bupdate<32><<<blocks, 256, 0, s>>>(n, mp, k, Z0, tm, nt, Y); break;
     }
     return cudaGetLastError();
+  }
+  // The (hi, lo) float copies of the update matrices, zero-padded to mp x mp, in the layout of
+  // SplitTerms::Ms; false when an entry is neither zero nor in [2^-80, 2^80] (the launch then runs
+  // natively). hi is the float nearest to v and lo the float nearest to v - hi, so hi + lo is within
+  // 2^-48 |v| of v.
+  bool split_matrices(const std::vector<std::pair<const double *, std::vector<double>>> &terms, float4 *out) const {
+    const int half = mp / 2;
+    for (size_t t = 0; t < terms.size(); ++t)
+      for (int p = 0; p < mp; ++p)
+        for (int j = 0; j < half; ++j) {
+          float hi[2], lo[2];
+          for (int c = 0; c < 2; ++c) {
+            const int col = 2 * j + c;
+            const double v = (p < k && col < k) ? terms[t].second[(size_t)p * k + col] : 0.0;
+            const double a = std::fabs(v);
+            if (v != 0.0 && !(a >= 0x1p-80 && a <= 0x1p80)) return false;
+            hi[c] = (float)v;
+            lo[c] = (float)(v - (double)hi[c]);
+          }
+          out[t * (size_t)mp * half + (size_t)p * half + j] = make_float4(hi[0], hi[1], lo[0], lo[1]);
+        }
+    return true;
   }
 };
 

@@ -107,3 +107,47 @@ def test_coupled_edge_columns_and_wide_block(ens):
     assert st["status"][9] == oracle.NONFINITE
     ok = [l for l in range(32) if l not in (5, 9)]
     assert np.all(st["status"][ok] == 0) and np.all(_true_relres(op, B[:, ok], X[:, ok]) <= 1.05e-8)
+
+
+@pytest.mark.parametrize("mode", ["native", "split"])
+def test_coupled_arithmetic_modes_match_oracle(ens, mode):
+    """The Gram products and block updates run as native DFMA or as split-float products (the
+    matrix's float64 mode); both meet the oracle's bars on a preconditioned solve with odd k."""
+    op = gen.cubes(48, 32, 24, size=4)
+    B = gen.rhs_normal(op.n, 5, 44, zero_mean=True)
+    tol = 1e-9
+    ref = oracle.block_solve(op, B, tol, precond="chebyshev")
+    with ens.Matrix.from_operator(op) as A:
+        A.set_f64_mode(mode)
+        X, st = ens.solve_block_coupled(A, torch.from_numpy(B).cuda(), tol=tol, precond="chebyshev")
+    _check(op, B, X.cpu().numpy(), st, ref, tol)
+
+
+@pytest.mark.parametrize("scale", [2.0**60, 2.0**-60])
+def test_coupled_values_outside_split_window(ens, scale):
+    """Right-hand sides scaled far outside the split window [2^-40, 2^44) send every row of the
+    updates and every Gram tile to native DFMA; the solve still meets the oracle's bars (the
+    oracle solves the scaled system)."""
+    op = gen.dirichlet_box(16)
+    B = gen.rhs_uniform(op.n, 4, 45) * scale
+    tol = 1e-9
+    ref = oracle.block_solve(op, B, tol)
+    with ens.Matrix.from_operator(op) as A:
+        A.set_f64_mode("split")
+        X, st = ens.solve_block_coupled(A, torch.from_numpy(B).cuda(), tol=tol)
+    _check(op, B, X.cpu().numpy(), st, ref, tol)
+
+
+def test_coupled_mixed_scales_across_columns(ens):
+    """Columns of very different magnitude: some rows fall back, others stay split, and the
+    fallback decision is per row group, so both paths meet within one update."""
+    op = gen.dirichlet_box(16)
+    B = gen.rhs_uniform(op.n, 4, 46)
+    B[:, 1] *= 2.0**50
+    B[: op.n // 2, 3] *= 2.0**-45
+    tol = 1e-9
+    ref = oracle.block_solve(op, B, tol)
+    with ens.Matrix.from_operator(op) as A:
+        A.set_f64_mode("split")
+        X, st = ens.solve_block_coupled(A, torch.from_numpy(B).cuda(), tol=tol)
+    _check(op, B, X.cpu().numpy(), st, ref, tol)
