@@ -410,6 +410,143 @@ def attach_oracle_errors(section: dict, keep: dict, refs: dict, sol_bar: float =
                                              "host_seconds": ref["seconds"]}
 
 
+# cuSPARSE generic-API constants (cusparse.h, library_types.h)
+_CUSPARSE_INDEX_32I, _CUSPARSE_BASE_ZERO, _CUSPARSE_NON_TRANSPOSE, _CUSPARSE_ORDER_ROW, _CUDA_R_64F = 2, 0, 0, 2, 1
+_CUSPARSE_SPMM_ALGS = {"default": 0, "csr_alg1": 4, "csr_alg2": 6, "csr_alg3": 12}
+_CUSPARSE_SPMV_ALGS = {"default": 0, "csr_alg1": 2, "csr_alg2": 3}
+
+
+def _load_cusparse():
+    import ctypes
+
+    for name in ("libcusparse.so", "libcusparse.so.13", "libcusparse.so.12", "/usr/local/cuda/lib64/libcusparse.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def cusparse_comparator(op, Xs, per_m_us, stream, reps: int = 20):
+    """External comparator only (never dispatched to): the vendor library's CSR x dense product on the
+    same operator and the same row-interleaved inputs, FP64, int32 indices, called directly through
+    cuSPARSE's generic API (SpMV at m = 1, SpMM with row-major dense blocks otherwise). Every
+    algorithm the library offers for the case is timed (CUDA events over `reps` calls after 3 warm-up
+    calls, work buffer and preprocessing outside the timed region) and the fastest is reported, with
+    its algorithmic GB/s, this library's speed-up over it and the largest element-wise difference of
+    the two Y relative to |A||X|."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    lib = _load_cusparse()
+    if lib is None:
+        return {"unavailable": "libcusparse not found"}
+    vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P = ctypes.POINTER(vp)
+    lib.cusparseCreate.argtypes = [P]
+    lib.cusparseSetStream.argtypes = [vp, vp]
+    lib.cusparseCreateCsr.argtypes = [P, i64, i64, i64, vp, vp, vp, ci, ci, ci, ci]
+    lib.cusparseCreateDnMat.argtypes = [P, i64, i64, i64, vp, ci, ci]
+    lib.cusparseCreateDnVec.argtypes = [P, i64, vp, ci]
+    lib.cusparseSpMM_bufferSize.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp, ci, ci, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cusparseSpMM_preprocess.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp, ci, ci, vp]
+    lib.cusparseSpMM.argtypes = [vp, ci, ci, vp, vp, vp, vp, vp, ci, ci, vp]
+    lib.cusparseSpMV_bufferSize.argtypes = [vp, ci, vp, vp, vp, vp, vp, ci, ci, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cusparseSpMV.argtypes = [vp, ci, vp, vp, vp, vp, vp, ci, ci, vp]
+    for f in ("cusparseDestroy", "cusparseDestroySpMat", "cusparseDestroyDnMat", "cusparseDestroyDnVec"):
+        getattr(lib, f).argtypes = [vp]
+
+    def ck(status, what):
+        if status != 0:
+            raise RuntimeError(f"{what}: cuSPARSE status {status}")
+
+    h, A = vp(), vp()
+    ck(lib.cusparseCreate(ctypes.byref(h)), "cusparseCreate")
+    ck(lib.cusparseSetStream(h, vp(stream.cuda_stream)), "cusparseSetStream")
+    rp = torch.from_numpy(op.row_ptr.astype(np.int32)).cuda()
+    cols = torch.from_numpy(op.col_idx.astype(np.int32)).cuda()
+    vals = torch.from_numpy(op.val).cuda()
+    ck(lib.cusparseCreateCsr(ctypes.byref(A), op.n, op.n, op.nnz, vp(rp.data_ptr()), vp(cols.data_ptr()),
+                             vp(vals.data_ptr()), _CUSPARSE_INDEX_32I, _CUSPARSE_INDEX_32I, _CUSPARSE_BASE_ZERO,
+                             _CUDA_R_64F), "cusparseCreateCsr")
+    alpha, beta = ctypes.c_double(1.0), ctypes.c_double(0.0)
+    pa, pb = ctypes.cast(ctypes.byref(alpha), vp), ctypes.cast(ctypes.byref(beta), vp)
+    absA = torch.sparse_csr_tensor(rp, cols, vals.abs(), size=(op.n, op.n))
+    out = {}
+    for m, X in Xs.items():
+        Y = torch.empty_like(X)
+        dx, dy = vp(), vp()
+        if m == 1:
+            ck(lib.cusparseCreateDnVec(ctypes.byref(dx), op.n, vp(X.data_ptr()), _CUDA_R_64F), "DnVec")
+            ck(lib.cusparseCreateDnVec(ctypes.byref(dy), op.n, vp(Y.data_ptr()), _CUDA_R_64F), "DnVec")
+            algs = _CUSPARSE_SPMV_ALGS
+        else:
+            ck(lib.cusparseCreateDnMat(ctypes.byref(dx), op.n, m, m, vp(X.data_ptr()), _CUDA_R_64F, _CUSPARSE_ORDER_ROW), "DnMat")
+            ck(lib.cusparseCreateDnMat(ctypes.byref(dy), op.n, m, m, vp(Y.data_ptr()), _CUDA_R_64F, _CUSPARSE_ORDER_ROW), "DnMat")
+            algs = _CUSPARSE_SPMM_ALGS
+        per_alg, best = {}, None
+        for name, alg in algs.items():
+            try:
+                size = ctypes.c_size_t(0)
+                if m == 1:
+                    ck(lib.cusparseSpMV_bufferSize(h, _CUSPARSE_NON_TRANSPOSE, pa, A, dx, pb, dy, _CUDA_R_64F, alg,
+                                                   ctypes.byref(size)), "SpMV_bufferSize")
+                else:
+                    ck(lib.cusparseSpMM_bufferSize(h, _CUSPARSE_NON_TRANSPOSE, _CUSPARSE_NON_TRANSPOSE, pa, A, dx, pb, dy,
+                                                   _CUDA_R_64F, alg, ctypes.byref(size)), "SpMM_bufferSize")
+                buf = torch.empty(max(int(size.value), 16), dtype=torch.uint8, device="cuda")
+                bp = vp(buf.data_ptr())
+                if m == 1:
+                    def call():
+                        ck(lib.cusparseSpMV(h, _CUSPARSE_NON_TRANSPOSE, pa, A, dx, pb, dy, _CUDA_R_64F, alg, bp), "SpMV")
+                else:
+                    lib.cusparseSpMM_preprocess(h, _CUSPARSE_NON_TRANSPOSE, _CUSPARSE_NON_TRANSPOSE, pa, A, dx, pb, dy,
+                                                _CUDA_R_64F, alg, bp)  # optional; only some algorithms use it
+
+                    def call():
+                        ck(lib.cusparseSpMM(h, _CUSPARSE_NON_TRANSPOSE, _CUSPARSE_NON_TRANSPOSE, pa, A, dx, pb, dy,
+                                            _CUDA_R_64F, alg, bp), "SpMM")
+                for _ in range(3):
+                    call()
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                s.record(stream)
+                for _ in range(reps):
+                    call()
+                e.record(stream)
+                torch.cuda.synchronize()
+                us = s.elapsed_time(e) / reps * 1e3
+                scale = torch.mm(absA, X.abs()) if m > 1 else torch.mv(absA, X.abs().reshape(-1)).reshape(-1, 1)
+                per_alg[name] = {"us": us, "Y": Y.clone(), "scale": scale}
+                if best is None or us < per_alg[best]["us"]:
+                    best = name
+            except RuntimeError as exc:
+                per_alg[name] = {"unavailable": str(exc)}
+        lib.cusparseDestroyDnMat(dx) if m > 1 else lib.cusparseDestroyDnVec(dx)
+        lib.cusparseDestroyDnMat(dy) if m > 1 else lib.cusparseDestroyDnVec(dy)
+        if best is None:
+            out[str(m)] = {"unavailable": per_alg}
+            continue
+        us = per_alg[best]["us"]
+        out[str(m)] = {
+            "us": us,
+            "algorithm": ("spmv_" if m == 1 else "spmm_") + best,
+            "us_per_algorithm": {k: v.get("us") for k, v in per_alg.items()},
+            "gbs": alg_bytes(op.n, op.nnz, m) / (us * 1e-6) / 1e9,
+            "ours_speedup": us / per_m_us[m],
+            "Y": per_alg[best]["Y"],
+            "scale": per_alg[best]["scale"],
+        }
+        for v in per_alg.values():
+            v.pop("Y", None)
+            v.pop("scale", None)
+    lib.cusparseDestroySpMat(A)
+    lib.cusparseDestroy(h)
+    return out
+
+
 def cubes_gspmv_metrics(reps: int = 20):
     """FP64 GSpMV on the wall-mounted-cube operator 192 x 128 x 96 (rows of 5-7 nonzeros) for
     m = 1..32, each width autotuned: device time per launch (CUDA events around `reps` launches
@@ -1109,6 +1246,18 @@ def main():
         "api": "ens_gspmv_host (pinned host X/Y)",
     }
 
+    # cuSPARSE SpMM on the same operator and inputs: context only, outside the timed region
+    comparator = cusparse_comparator(op, Xs, per_m_us, stream) if rank == 0 else None
+    if comparator is not None and "unavailable" not in comparator:
+        for m in M_SWEEP:
+            c = comparator.get(str(m))
+            if not c or "Y" not in c:
+                continue
+            ens.gspmv(A, Xs[m], Ys[m], stream=stream)
+            diff = ((c.pop("Y") - Ys[m]).abs() / c.pop("scale").clamp_min(1e-300)).max().item()
+            c["max_rel_diff_vs_ours"] = diff
+        torch.cuda.empty_cache()
+
     keep_solves, keep_batch, keep_serving = {}, {}, {}
     solves = None if args.no_solves else solve_metrics(keep=keep_solves)
     projection = None if args.no_solves else projection_metrics()
@@ -1171,6 +1320,7 @@ def main():
             "roofline": roofline,
             "sweep": sweep,
             "e2e": e2e,
+            "cusparse_spmm": comparator,
             "solves": solves,
             "projection": projection,
             "cubes_gspmv": cubes,
