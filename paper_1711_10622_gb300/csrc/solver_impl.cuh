@@ -711,6 +711,86 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// The coarsest level's whole smoothing z = S_steps(src) in one block (levels of at most
+// kCoarseBlockRows rows): the first term of k_amg_first and then every step of k_cheb, with a block
+// barrier where the separate launches had a kernel boundary. A step's product reads the previous
+// step's d, written in this launch, so X is loaded with plain (coherent) loads and multiplied with
+// native FMA (float values for the float32 solver): a few thousand products per step, where one
+// launch per step cost more than its work.
+constexpr int kCoarseBlockRows = 2048;
+constexpr int kMaxCoarseSteps = 64;
+template <typename T>
+struct CoarseCoefs {
+  T c1[kMaxCoarseSteps], c2[kMaxCoarseSteps];  // step k >= 1
+};
+
+template <typename Arith, int VEC, int LANES>
+__global__ void __launch_bounds__(kThreads)
+    k_amg_coarse(MatView A, int32_t m, const typename Arith::T *__restrict__ src, typename Arith::T *da,
+                 typename Arith::T *db, typename Arith::T *res, typename Arith::T *z, typename Arith::T inv_theta,
+                 CoarseCoefs<typename Arith::T> cf, int32_t steps) {
+  using T = typename Arith::T;
+  constexpr int G = kThreads / LANES;
+  const int32_t c = (threadIdx.x % LANES) * VEC;
+  const bool act = c < m;
+  if (act)
+    for (int64_t i = threadIdx.x / LANES; i < A.n; i += G) {
+      T sv[VEC];
+      load_vec<T, VEC>(src + i * m + c, sv);
+      const T sc = Arith::dinv(A, i) * inv_theta;
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) sv[q] *= sc;
+      store_vec<T, VEC>(da + i * m + c, sv);
+      store_vec<T, VEC>(z + i * m + c, sv);
+    }
+  __syncthreads();
+  T *din = da, *dout = db;
+  for (int k = 1; k < steps; ++k) {
+    const bool first = k == 1, last = k == steps - 1;
+    const T c1 = cf.c1[k], c2 = cf.c2[k];
+    if (act)
+      for (int64_t i = threadIdx.x / LANES; i < A.n; i += G) {
+        T w[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) w[q] = T(0);
+        for (int32_t j = A.rp[i]; j < A.rp[i + 1]; ++j) {
+          T a;
+          if constexpr (std::is_same<T, float>::value)
+            a = A.val32[j];
+          else
+            a = A.val[j];
+          T x[VEC];
+          load_vec_rw<T, VEC>(din + (int64_t)A.ci[j] * m + c, x);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) w[q] = fma(a, x[q], w[q]);
+        }
+        T di[VEC], rs[VEC], zv[VEC], dn[VEC];
+        load_vec_rw<T, VEC>(din + i * m + c, di);
+        if (first)
+          load_vec<T, VEC>(src + i * m + c, rs);
+        else
+          load_vec_rw<T, VEC>(res + i * m + c, rs);
+        load_vec_rw<T, VEC>(z + i * m + c, zv);
+        const T dv = Arith::dinv(A, i);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          rs[q] -= w[q];
+          dn[q] = c1 * di[q] + c2 * (dv * rs[q]);
+          zv[q] += dn[q];
+        }
+        store_vec<T, VEC>(z + i * m + c, zv);
+        if (!last) {
+          store_vec<T, VEC>(res + i * m + c, rs);
+          store_vec<T, VEC>(dout + i * m + c, dn);
+        }
+      }
+    __syncthreads();
+    T *t = din;
+    din = dout;
+    dout = t;
+  }
+}
+
 // res = r - A z
 template <typename Arith, int VEC, int LANES>
 __global__ void ENS_LIGHT_BOUNDS(Arith)
@@ -901,6 +981,21 @@ struct AmgCycle {
   void level_cycle(size_t l, const T *r, T *z, cudaStream_t st) {
     const Level &L = lev[l];
     if (l + 1 == lev.size()) {
+      if (L.n <= kCoarseBlockRows && o.coarse_steps <= kMaxCoarseSteps) {  // one block, one launch
+        const double theta = 0.5 * (o.cheb_hi + o.cheb_lo), delta = 0.5 * (o.cheb_hi - o.cheb_lo);
+        const double sigma = theta / delta;
+        double rho_prev = 1.0 / sigma;
+        CoarseCoefs<T> cf{};
+        for (int k = 1; k < o.coarse_steps; ++k) {
+          const double rho = 1.0 / (2.0 * sigma - rho_prev);
+          cf.c1[k] = (T)(rho * rho_prev);
+          cf.c2[k] = (T)(2.0 * rho / delta);
+          rho_prev = rho;
+        }
+        k_amg_coarse<Ar, V, Ln><<<1, kThreads, 0, st>>>(L.A, mp, r, L.da, L.db, L.cres, z, (T)(1.0 / theta), cf,
+                                                        o.coarse_steps);
+        return;
+      }
       this->template smooth<Ar, V, Ln>(L, r, z, false, o.coarse_steps, st);
       return;
     }
