@@ -314,7 +314,7 @@ __device__ __forceinline__ int gram_real_col(int jj, int ld, int q1, int q2) {
 // computed with native DFMA.
 // EPT: entry pairs per thread the kernel is compiled for (1 when np <= 256, else 4).
 template <int EPT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, EPT == 1 ? 4 : 2)
     k_gram_split(int64_t n, int32_t ld, int32_t k, const double *__restrict__ U, const double *__restrict__ W1,
                  int32_t q1, const double *__restrict__ W2, int32_t q2, double *__restrict__ partials) {
   __shared__ uint64_t st_hi[kGramStage / 2 + 96], st_lo[kGramStage / 2 + 96];
@@ -326,7 +326,10 @@ __global__ void __launch_bounds__(256)
   const int ept = np > 256 ? (np + 255) / 256 : 1;  // <= EPT (k <= 32, qp <= 64)
   const int slice = np >= 256 ? 0 : (int)threadIdx.x / np;
   const bool active = slice < S;
-  // this thread's three staged elements: source column pointer, tile row, float slot in the stage
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(n, r0 + per);
+  // this thread's three staged elements: source pointer (advanced by one tile per step), tile row,
+  // float slot in the stage
   const double *src[3];
   int srow[3], sslot[3];
 #pragma unroll
@@ -334,8 +337,23 @@ __global__ void __launch_bounds__(256)
     const int v = (int)threadIdx.x + u * 256;
     const int r = v / w, c = v % w;
     srow[u] = v < R * w ? r : R;  // R: no element
-    src[u] = c < ld ? U + c : (c < ld + q1p ? W1 + (c - ld) : W2 + (c - ld - q1p));
+    const double *col = c < ld ? U + c : (c < ld + q1p ? W1 + (c - ld) : W2 + (c - ld - q1p));
+    src[u] = col + (r0 + (srow[u] < R ? r : 0)) * ld;
     sslot[u] = (c * RPs + r / 2) * 2 + (r & 1);
+  }
+  const int64_t tile_step = (int64_t)R * ld;
+  // this thread's entry pairs: stage offsets of its U column and its two W columns
+  int eoff_u[EPT], eoff_a[EPT], eoff_b[EPT], ei[EPT], ej[EPT];
+  bool eon[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int e = (np >= 256 ? (int)threadIdx.x + u * 256 : (int)threadIdx.x % np);
+    eon[u] = active && u < ept && e < np;
+    ei[u] = eon[u] ? e / hp : 0;
+    ej[u] = eon[u] ? e % hp : 0;
+    eoff_u[u] = ei[u] * RPs;
+    eoff_a[u] = (ld + ej[u]) * RPs;
+    eoff_b[u] = (ld + ej[u] + hp) * RPs;
   }
   uint64_t ah[EPT], al[EPT], bh[EPT], bl[EPT];
   double nat[EPT][2];
@@ -344,15 +362,12 @@ __global__ void __launch_bounds__(256)
     ah[u] = al[u] = bh[u] = bl[u] = 0;
     nat[u][0] = nat[u][1] = 0.0;
   }
-  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(n, r0 + per);
   double x[3];
-  auto fetch = [&](int64_t base) {
-    const int rows = (int)min((int64_t)R, r1 - base);
+  auto fetch = [&](int rows) {
 #pragma unroll
-    for (int u = 0; u < 3; ++u) x[u] = srow[u] < rows ? src[u][(base + srow[u]) * ld] : 0.0;
+    for (int u = 0; u < 3; ++u) x[u] = srow[u] < rows ? *src[u] : 0.0;
   };
-  if (r0 < r1) fetch(r0);
+  if (r0 < r1) fetch((int)min((int64_t)R, r1 - r0));
   float *fh = reinterpret_cast<float *>(st_hi), *fl = reinterpret_cast<float *>(st_lo);
   for (int64_t base = r0; base < r1; base += R) {
     const int rows = (int)min((int64_t)R, r1 - base);
@@ -365,25 +380,26 @@ __global__ void __launch_bounds__(256)
         split_f64(x[u], fh[sslot[u]], fl[sslot[u]]);
       }
     const bool tile_bad = __syncthreads_or(bad) != 0;
-    if (base + R < r1) fetch(base + R);
-    if (!active) continue;
+    if (base + R < r1) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) src[u] += tile_step;
+      fetch((int)min((int64_t)R, r1 - base - R));
+    }
     const int rps = (rows + 1) / 2;
 #pragma unroll
     for (int u = 0; u < EPT; ++u) {
-      const int e = (np >= 256 ? (int)threadIdx.x + u * 256 : (int)threadIdx.x % np);
-      if (u >= ept || e >= np) break;
-      const int i = e / hp, j = e % hp;
+      if (!eon[u]) break;
       if (!tile_bad) {
-        const uint64_t *uh = st_hi + i * RPs, *ul = st_lo + i * RPs;
-        const uint64_t *wah = st_hi + (ld + j) * RPs, *wal = st_lo + (ld + j) * RPs;
-        const uint64_t *wbh = st_hi + (ld + j + hp) * RPs, *wbl = st_lo + (ld + j + hp) * RPs;
+        const uint64_t *uh = st_hi + eoff_u[u], *ul = st_lo + eoff_u[u];
+        const uint64_t *wah = st_hi + eoff_a[u], *wal = st_lo + eoff_a[u];
+        const uint64_t *wbh = st_hi + eoff_b[u], *wbl = st_lo + eoff_b[u];
         for (int rp = slice; rp < rps; rp += S) {
           const uint64_t xh = uh[rp], xl = ul[rp];
           acc_pair(xh, xl, wah[rp], wal[rp], ah[u], al[u]);
           acc_pair(xh, xl, wbh[rp], wbl[rp], bh[u], bl[u]);
         }
       } else {
-        const int ja = j, jb = j + hp;
+        const int ja = ej[u], jb = ej[u] + hp, i = ei[u];
         const double *Wa = ja < q1p ? W1 + ja : W2 + (ja - q1p);
         const double *Wb = jb < q1p ? W1 + jb : W2 + (jb - q1p);
         for (int rp = slice; rp < rps; rp += S)
@@ -403,15 +419,13 @@ __global__ void __launch_bounds__(256)
   const int q = q1 + q2;
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
-    const int e = (np >= 256 ? (int)threadIdx.x + u * 256 : (int)threadIdx.x % np);
-    if (u >= ept || !active || e >= np) break;
+    if (!eon[u]) break;
     const double va = (pair_value(ah[u], al[u], 0) + pair_value(ah[u], al[u], 1)) + nat[u][0];
     const double vb = (pair_value(bh[u], bl[u], 0) + pair_value(bh[u], bl[u], 1)) + nat[u][1];
     if (S == 1) {
-      const int i = e / hp, j = e % hp;
-      const int ca = gram_real_col(j, ld, q1, q2), cb = gram_real_col(j + hp, ld, q1, q2);
-      if (ca >= 0) partials[(int64_t)blockIdx.x * k * q + i * q + ca] = va;
-      if (cb >= 0) partials[(int64_t)blockIdx.x * k * q + i * q + cb] = vb;
+      const int ca = gram_real_col(ej[u], ld, q1, q2), cb = gram_real_col(ej[u] + hp, ld, q1, q2);
+      if (ca >= 0) partials[(int64_t)blockIdx.x * k * q + ei[u] * q + ca] = va;
+      if (cb >= 0) partials[(int64_t)blockIdx.x * k * q + ei[u] * q + cb] = vb;
     } else {
       red[2 * threadIdx.x] = va;
       red[2 * threadIdx.x + 1] = vb;
