@@ -29,38 +29,58 @@ inline int64_t flat_stride(int64_t threads, int32_t m) { return threads / m * m;
 
 int grid_for_elems(int64_t elems, int sms) {
   const int64_t want = (elems + kThreads - 1) / kThreads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
 }
 
 // Pass 1: per block, per pair and column, the sum of X*Y over the elements this block's threads
 // visit, accumulated per thread in flat-index order and then over the block's threads in thread
-// order (fixed order: deterministic). partials[b][k*m + l].
+// order (fixed order: deterministic). partials[b][k*m + l]. NP pairs; the loads of four strided
+// elements are issued before their products, which are then added in the same order as one at a
+// time (the same bits, more loads in flight).
+template <int NP>
 __global__ void __launch_bounds__(kThreads)
-    k_dots_partial(int64_t total, int32_t m, int32_t npairs, Ptrs4 X, Ptrs4 Y, int64_t stride, double *partials) {
-  __shared__ double sm[kMaxPairs][kThreads];
+    k_dots_partial(int64_t total, int32_t m, Ptrs4 X, Ptrs4 Y, int64_t stride, double *partials) {
+  constexpr int U = 4;
+  __shared__ double sm[NP][kThreads];
   const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  double acc[kMaxPairs] = {0.0, 0.0, 0.0, 0.0};
-  if (t < stride) {
-    for (int64_t e = t; e < total; e += stride) {
+  double acc[NP];
 #pragma unroll
-      for (int k = 0; k < kMaxPairs; ++k)
-        if (k < npairs) acc[k] = fma(__ldg(X.p[k] + e), __ldg(Y.p[k] + e), acc[k]);
+  for (int k = 0; k < NP; ++k) acc[k] = 0.0;
+  if (t < stride) {
+    int64_t e = t;
+    for (; e + (U - 1) * stride < total; e += U * stride) {
+      double x[U][NP], y[U][NP];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          x[u][k] = __ldg(X.p[k] + e + u * stride);
+          y[u][k] = __ldg(Y.p[k] + e + u * stride);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) acc[k] = fma(x[u][k], y[u][k], acc[k]);
+    }
+    for (; e < total; e += stride) {
+#pragma unroll
+      for (int k = 0; k < NP; ++k) acc[k] = fma(__ldg(X.p[k] + e), __ldg(Y.p[k] + e), acc[k]);
     }
   }
 #pragma unroll
-  for (int k = 0; k < kMaxPairs; ++k) sm[k][threadIdx.x] = acc[k];
+  for (int k = 0; k < NP; ++k) sm[k][threadIdx.x] = acc[k];
   __syncthreads();
-  // thread j < npairs*m sums column l = j % m of pair k = j / m over the threads of this block that
+  // thread j < NP*m sums column l = j % m of pair k = j / m over the threads of this block that
   // own column l, in thread order
   const int64_t base = (int64_t)blockIdx.x * kThreads;
-  for (int j = threadIdx.x; j < npairs * m; j += kThreads) {
+  for (int j = threadIdx.x; j < NP * m; j += kThreads) {
     const int k = j / m, l = j % m;
     // first thread of this block whose global index is congruent to l modulo m
     int first = (int)((l - base % m + m) % m);
     double s = 0.0;
     for (int u = first; u < kThreads; u += m)
       if (base + u < stride) s += sm[k][u];
-    partials[(int64_t)blockIdx.x * npairs * m + j] = s;
+    partials[(int64_t)blockIdx.x * NP * m + j] = s;
   }
 }
 
@@ -138,7 +158,12 @@ ens_status ens_block_dots(int64_t n, int32_t m, int32_t npairs, const double *co
   const int64_t stride = flat_stride((int64_t)grid * kThreads, m);
   double *partials = nullptr;
   ENS_CUDA_TRY(cudaMallocAsync(&partials, (size_t)grid * npairs * m * sizeof(double), s));
-  k_dots_partial<<<grid, kThreads, 0, s>>>(total, m, npairs, px, py, stride, partials);
+  switch (npairs) {
+    case 1: k_dots_partial<1><<<grid, kThreads, 0, s>>>(total, m, px, py, stride, partials); break;
+    case 2: k_dots_partial<2><<<grid, kThreads, 0, s>>>(total, m, px, py, stride, partials); break;
+    case 3: k_dots_partial<3><<<grid, kThreads, 0, s>>>(total, m, px, py, stride, partials); break;
+    default: k_dots_partial<4><<<grid, kThreads, 0, s>>>(total, m, px, py, stride, partials); break;
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     k_partials_final<<<partials_final_grid(npairs * m), 256, 0, s>>>(grid, npairs * m, partials, out);
