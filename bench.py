@@ -1190,7 +1190,8 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    per_m_us = {m: 1e3 * statistics.fmean(e[m][0].elapsed_time(e[m][1]) for e in evs) for m in M_SWEEP}
+    per_m_all = {m: [1e3 * e[m][0].elapsed_time(e[m][1]) for e in evs] for m in M_SWEEP}
+    per_m_us = {m: statistics.fmean(v) for m, v in per_m_all.items()}
     bytes_step = sum(alg_bytes(n, nnz, m) for m in M_SWEEP)
     sec, bps = replica_throughput(dist, start.elapsed_time(end) * 1e-3, bytes_step, K)
     ms, value = sec * 1e3, bps / 1e9
@@ -1213,6 +1214,8 @@ def main():
     sweep = {
         str(m): {
             "us": per_m_us[m],
+            "us_median": statistics.median(per_m_all[m]),
+            "us_min": min(per_m_all[m]),
             "gbs": alg_bytes(n, nnz, m) / (per_m_us[m] * 1e-6) / 1e9,
             "frac_of_measured_peak": alg_bytes(n, nnz, m) / (per_m_us[m] * 1e-6) / 1e9 / peak,
             "alg_mb": alg_bytes(n, nnz, m) / 1e6,
