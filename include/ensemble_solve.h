@@ -141,9 +141,10 @@ ens_status ens_gspmv(const ens_matrix *A, int32_t m, int32_t dtype, const void *
  * The same product with HOST buffers X (n*m, read) and Y (n*m, written). The library copies X to
  * a device staging buffer it owns, runs the product and copies Y back; synchronous (returns after
  * Y is written). Page-locked host memory gives the full copy bandwidth. On matrices of more than
- * one 256-row tile the three stages overlap: X arrives in row prefixes on a library-owned copy
- * stream, each row chunk is computed on `stream` once the X rows its column indices reach have
- * arrived, and its Y rows are copied back on a second library-owned stream. The overlap needs
+ * one 256-row tile the three stages overlap: X arrives in blocks of rows on a library-owned copy
+ * stream, in the order the row chunks (up to 16) first need them, each row chunk is computed on
+ * `stream` once the X blocks its column indices reach have arrived (periodic couplings included),
+ * and its Y rows are copied back on a second library-owned stream. The overlap needs
  * page-locked X and Y: with pageable buffers each copy call returns only when it is done, so the
  * copies and kernels then run largely one after another. Y holds the same
  * values as ens_gspmv's to within the accuracy bound below (the FP64 split/native assignment of

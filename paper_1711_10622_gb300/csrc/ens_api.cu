@@ -202,17 +202,21 @@ ens_status ens::create_matrix(int64_t n, int64_t ncols, int64_t nnz, const int32
   A->split_ok = (hflags & 1u) == 0;
   A->full_diag = (hflags & 2u) == 0;
   // Row chunks of the pipelined host-buffer product: up to kPipeChunks chunks of whole tiles, each
-  // with the prefix maximum of its column indices (the X rows it needs).
+  // with the set of X row blocks its column indices reach.
   {
     const int64_t tiles = (n + kPipeAlignRows - 1) / kPipeAlignRows;
     const int64_t chunks = std::min<int64_t>(kPipeChunks, tiles);
     const int64_t per = (tiles + chunks - 1) / chunks * kPipeAlignRows;
-    int64_t need = 0;
+    A->pipe_block_rows = std::max<int64_t>(1, (ncols + kPipeBlocks - 1) / kPipeBlocks);
     for (int64_t r0 = 0; r0 < n; r0 += per) {
       const int64_t r1 = std::min<int64_t>(n, r0 + per);
-      for (int64_t j = row_ptr[r0]; j < row_ptr[r1]; ++j) need = std::max<int64_t>(need, (int64_t)col_idx[j] + 1);
+      uint64_t mask[kPipeMaskWords] = {};
+      for (int64_t j = row_ptr[r0]; j < row_ptr[r1]; ++j) {
+        const int64_t b = (int64_t)col_idx[j] / A->pipe_block_rows;
+        mask[b / 64] |= 1ull << (b % 64);
+      }
       A->pipe_row.push_back(r0);
-      A->pipe_need.push_back(need);
+      A->pipe_mask.insert(A->pipe_mask.end(), mask, mask + kPipeMaskWords);
     }
     A->pipe_row.push_back(n);
   }
@@ -362,13 +366,26 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
   e = cudaEventRecord(ev_start, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(A->pipe_h2d, ev_start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(A->pipe_d2h, ev_start, 0);
-  int64_t have = 0;
+  // X blocks in the order the chunks first need them, each maximal run of new blocks as one copy
+  uint64_t have[kPipeMaskWords] = {};
+  const int64_t brows = A->pipe_block_rows, nblocks = (A->n + brows - 1) / brows;
   for (int64_t k = 0; k < chunks && e == cudaSuccess; ++k) {
-    const int64_t need = A->pipe_need[k];
-    if (need > have)
-      e = cudaMemcpyAsync(dx + have * row_bytes, hx + have * row_bytes, (need - have) * row_bytes, cudaMemcpyHostToDevice,
+    const uint64_t *need = A->pipe_mask.data() + k * kPipeMaskWords;
+    int64_t b = 0;
+    while (b < nblocks && e == cudaSuccess) {
+      const bool want = ((need[b / 64] & ~have[b / 64]) >> (b % 64)) & 1ull;
+      if (!want) {
+        ++b;
+        continue;
+      }
+      int64_t b1 = b;
+      while (b1 < nblocks && (((need[b1 / 64] & ~have[b1 / 64]) >> (b1 % 64)) & 1ull)) ++b1;
+      const int64_t r0 = b * brows, r1 = std::min<int64_t>(A->n, b1 * brows);
+      e = cudaMemcpyAsync(dx + r0 * row_bytes, hx + r0 * row_bytes, (r1 - r0) * row_bytes, cudaMemcpyHostToDevice,
                           A->pipe_h2d);
-    have = std::max(have, need);
+      b = b1;
+    }
+    for (int w = 0; w < kPipeMaskWords; ++w) have[w] |= need[w];
     if (e == cudaSuccess) e = cudaEventRecord(ev_x[k], A->pipe_h2d);
   }
   // All chunk kernels are queued before any device-to-host copy: with pageable Y a copy call

@@ -45,11 +45,15 @@ struct ens_matrix {
   // staging buffers of ens_gspmv_host (grown on demand)
   void *stage_x = nullptr, *stage_y = nullptr;
   size_t stage_bytes = 0;
-  // ens_gspmv_host pipeline: row chunk k = rows [pipe_row[k], pipe_row[k+1]) reads X rows
-  // [0, pipe_need[k]) only (prefix maximum of its column indices + 1), so it can run as soon as
-  // that prefix of X has arrived, while later X rows are still being copied in and earlier Y rows
-  // copied out. Streams and events are created by the first pipelined call.
-  std::vector<int64_t> pipe_row, pipe_need;
+  // ens_gspmv_host pipeline: X rows are split into blocks of pipe_block_rows rows, and row chunk
+  // k = rows [pipe_row[k], pipe_row[k+1]) reads only the blocks whose bits are set in
+  // pipe_mask[k * kPipeMaskWords ...] (from its column indices). X is copied in block runs in the
+  // order the chunks first need them, so chunk k runs as soon as its blocks have arrived (with
+  // periodic or other wrap-around couplings too), while later blocks are still being copied in and
+  // earlier Y rows copied out. Streams and events are created by the first pipelined call.
+  std::vector<int64_t> pipe_row;
+  std::vector<uint64_t> pipe_mask;
+  int64_t pipe_block_rows = 1;
   cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
   std::vector<cudaEvent_t> pipe_ev;
   // aggregation multigrid hierarchy (ens_amg_setup), owned
@@ -106,7 +110,9 @@ ens_status autotune(ens_matrix *A, int m, int dtype, cudaStream_t s, int32_t *la
 ens_status launch_gspmv(const ens_matrix *A, int m, int dtype, const void *X, void *Y, cudaStream_t s);
 // Pipelined ens_gspmv_host: at most kPipeChunks row chunks, each a multiple of kPipeAlignRows rows
 // (a multiple of the GSpMV tile).
-constexpr int64_t kPipeChunks = 8;
+constexpr int64_t kPipeChunks = 16;
+constexpr int64_t kPipeBlocks = 128;  // X row blocks tracked per chunk
+constexpr int64_t kPipeMaskWords = kPipeBlocks / 64;
 constexpr int64_t kPipeAlignRows = 256;
 // The product for rows [r0, r1) only (r0 a multiple of 256): Y rows r0..r1-1, reading X anywhere.
 ens_status launch_gspmv_rows(const ens_matrix *A, int m, int dtype, const void *X, void *Y, int64_t r0, int64_t r1,
