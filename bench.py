@@ -1233,10 +1233,13 @@ def main():
     for m in M_SWEEP:  # warm the staging buffers
         ens.gspmv_host(A, hx[m], hy[m], stream=stream)
     barrier()
+    e2e_ms = {m: 0.0 for m in M_SWEEP}
     t0 = time.perf_counter()
     for _ in range(KE):
         for m in M_SWEEP:
+            tm = time.perf_counter()
             ens.gspmv_host(A, hx[m], hy[m], stream=stream)
+            e2e_ms[m] += (time.perf_counter() - tm) * 1e3 / KE
     torch.cuda.synchronize()
     te, e2e_bps = replica_throughput(dist, time.perf_counter() - t0, bytes_step, KE)
     io_bytes = sum(8 * n * m for m in M_SWEEP)
@@ -1246,6 +1249,7 @@ def main():
         "h2d_bytes_per_step": io_bytes,
         "d2h_bytes_per_step": io_bytes,
         "steps": KE,
+        "ms_per_m": {str(m): e2e_ms[m] for m in M_SWEEP},
         "api": "ens_gspmv_host (pinned host X/Y)",
     }
 
