@@ -226,9 +226,9 @@ def test_gspmv_host_buffers(ens):
 
 @pytest.mark.parametrize("m,dt", [(1, np.float64), (8, np.float64), (32, np.float64), (5, np.float64), (8, np.float32)])
 def test_gspmv_host_pipelined(ens, m, dt):
-    """ens_gspmv_host on an operator of 140 tiles: X arrives in prefixes, 8 row chunks run as their
-    prefixes land and their Y rows are copied out while later chunks compute; every row against
-    the definition (FP64 bound 1e-12 of |A||X|, FP32 bound (L+2) 2^-24)."""
+    """ens_gspmv_host on an operator of 140 tiles: X arrives in row blocks, up to 16 row chunks run
+    as the blocks they read land and their Y rows are copied out while later chunks compute; every
+    row against the definition (FP64 bound 1e-12 of |A||X|, FP32 bound (L+2) 2^-24)."""
     op = _op("cubes48x32x24")
     X = gen.rhs_normal(op.n, m, 600 + m).astype(dt)
     with ens.Matrix.from_operator(op) as A:
@@ -239,6 +239,18 @@ def test_gspmv_host_pipelined(ens, m, dt):
         _check_f64(op, X, Y)
     else:
         _check_f32(op, X, Y)
+
+
+@pytest.mark.parametrize("m", [1, 4, 16])
+def test_gspmv_host_pipelined_periodic(ens, m):
+    """A channel operator periodic in x and z: the first row chunk reads the last z-planes of X (the
+    wrap-around coupling), so its X blocks are not a prefix; every row against the definition."""
+    op = gen.channel(32, 16, 64)
+    assert op.n // 256 >= 16  # at least 16 row chunks
+    X = gen.rhs_normal(op.n, m, 700 + m)
+    with ens.Matrix.from_operator(op) as A:
+        Y = ens.gspmv_host(A, X)
+    _check_f64(op, X, Y)
 
 
 def test_gspmv_host_in_place(ens):
