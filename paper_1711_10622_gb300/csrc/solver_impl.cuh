@@ -88,8 +88,9 @@ struct LightBlocks {
   static constexpr int value = std::is_same<Arith, ArithF32>::value ? 8 : TileBlocks<Arith>::value;
 };
 #define ENS_LIGHT_BOUNDS(Arith) __launch_bounds__(kThreads, LightBlocks<Arith>::value)
-// The Chebyshev step with four columns per lane in split float64 (solver_cheb4.cu) needs 48
-// registers, as the standalone four-column GSpMV: 5 blocks per SM; every other form as LightBlocks.
+// The Chebyshev step and the V-cycle's residual and two-update smoothing with four columns per lane
+// in split float64 (solver_cheb4.cu) need 48 registers, as the standalone four-column GSpMV: 5 blocks
+// per SM; every other form as LightBlocks.
 template <typename Arith, int VEC>
 struct ChebBlocks {
   static constexpr int value =
@@ -253,6 +254,13 @@ __global__ void __launch_bounds__(kThreads, ChebBlocks<Arith, VEC>::value)
 bool launch_cheb4_split(int lanes4, bool first, bool last, const MatView &A, int32_t m, const double *din,
                         double *dout, const double *src, double *res, double *z, double c1, double c2,
                         uint32_t mask, int num_sms, int64_t grid_cap, cudaStream_t st);
+// The V-cycle's res = r - A z (k_amg_resid) and two-update smoothing (k_amg_smooth2) in the same
+// four-column form; false (nothing launched) for other lane counts.
+bool launch_amg_resid4_split(int lanes4, const MatView &A, int32_t m, const double *z, const double *r, double *res,
+                             uint32_t mask, int num_sms, int64_t grid_cap, cudaStream_t st);
+bool launch_amg_smooth2_4_split(int lanes4, bool add, const MatView &As, const MatView &A, int32_t m, const double *src,
+                                double *z, double inv_theta, double c1, double c2, uint32_t mask, int num_sms,
+                                int64_t grid_cap, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- v = A ph
 template <typename Arith, int VEC, int LANES>
@@ -808,7 +816,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // res = r - A z
 template <typename Arith, int VEC, int LANES>
-__global__ void ENS_LIGHT_BOUNDS(Arith)
+__global__ void __launch_bounds__(kThreads, ChebBlocks<Arith, VEC>::value)
     k_amg_resid(MatView A, int32_t m, const typename Arith::T *__restrict__ z, const typename Arith::T *__restrict__ r,
                 typename Arith::T *__restrict__ res, uint32_t mask) {
   using T = typename Arith::T;
@@ -826,7 +834,7 @@ __global__ void ENS_LIGHT_BOUNDS(Arith)
 //   d0 = D^-1 src / theta,  res1 = src - (As src) / theta,  d1 = c1 d0 + c2 D^-1 res1,
 //   z = d0 + d1  (ADD: z += d0 + d1).
 template <typename Arith, int VEC, int LANES, bool ADD>
-__global__ void ENS_LIGHT_BOUNDS(Arith)
+__global__ void __launch_bounds__(kThreads, ChebBlocks<Arith, VEC>::value)
     k_amg_smooth2(MatView As, MatView A, int32_t m, const typename Arith::T *__restrict__ src, typename Arith::T *z,
                   typename Arith::T inv_theta, typename Arith::T c1, typename Arith::T c2, uint32_t mask) {
   using T = typename Arith::T;
@@ -963,6 +971,11 @@ struct AmgCycle {
           return;
         }
       }
+      if constexpr (std::is_same<Ar, ArithF64Split>::value && V == 2 && Ln >= 2) {
+        if (mp % 4 == 0 && launch_amg_smooth2_4_split(Ln / 2, add, L.As, L.A, mp, src, z, it, c1, c2, L.as_mask, L.sms,
+                                                      (L.n + kTileRows - 1) / kTileRows, st))
+          return;
+      }
       if (add)
         k_amg_smooth2<Ar, V, Ln, true><<<L.grid, kThreads, 0, st>>>(L.As, L.A, mp, src, z, it, c1, c2, L.as_mask);
       else
@@ -1001,6 +1014,17 @@ struct AmgCycle {
     }
   }
 
+  // L.res = r - A z on level L
+  template <typename Ar, int V, int Ln>
+  void resid(const Level &L, const T *z, const T *r, cudaStream_t st) {
+    if constexpr (std::is_same<Ar, ArithF64Split>::value && V == 2 && Ln >= 2) {
+      if (mp % 4 == 0 &&
+          launch_amg_resid4_split(Ln / 2, L.A, mp, z, r, L.res, L.mask, L.sms, (L.n + kTileRows - 1) / kTileRows, st))
+        return;
+    }
+    k_amg_resid<Ar, V, Ln><<<L.grid, kThreads, 0, st>>>(L.A, mp, z, r, L.res, L.mask);
+  }
+
   template <typename Ar, int V, int Ln>
   void level_cycle(size_t l, const T *r, T *z, cudaStream_t st) {
     const Level &L = lev[l];
@@ -1025,11 +1049,11 @@ struct AmgCycle {
     }
     const Level &C = lev[l + 1];
     this->template smooth<Ar, V, Ln>(L, r, z, false, o.smooth_steps, st);
-    k_amg_resid<Ar, V, Ln><<<L.grid, kThreads, 0, st>>>(L.A, mp, z, r, L.res, L.mask);
+    this->template resid<Ar, V, Ln>(L, z, r, st);
     k_amg_restrict<T, V, Ln><<<L.cgrid, kThreads, 0, st>>>(L.nc, mp, L.ptr, L.mem, L.res, C.r);
     this->template cycle<V, Ln>(l + 1, C.r, C.z, st);
     k_amg_prolong<T, V, Ln><<<L.egrid, kThreads, 0, st>>>(L.n, mp, L.agg, C.z, z);
-    k_amg_resid<Ar, V, Ln><<<L.grid, kThreads, 0, st>>>(L.A, mp, z, r, L.res, L.mask);
+    this->template resid<Ar, V, Ln>(L, z, r, st);
     this->template smooth<Ar, V, Ln>(L, L.res, z, true, o.smooth_steps, st);
   }
 
