@@ -1223,12 +1223,15 @@ def main():
         ens.gspmv_host(A, hx[m], hy[m], stream=stream)
     barrier()
     e2e_ms = {m: 0.0 for m in M_SWEEP}
+    e2e_steps = []
     t0 = time.perf_counter()
     for _ in range(KE):
+        ts = time.perf_counter()
         for m in M_SWEEP:
             tm = time.perf_counter()
             ens.gspmv_host(A, hx[m], hy[m], stream=stream)
             e2e_ms[m] += (time.perf_counter() - tm) * 1e3 / KE
+        e2e_steps.append((time.perf_counter() - ts) * 1e3)
     torch.cuda.synchronize()
     te, e2e_bps = replica_throughput(dist, time.perf_counter() - t0, bytes_step, KE)
     io_bytes = sum(8 * n * m for m in M_SWEEP)
@@ -1239,6 +1242,11 @@ def main():
         "d2h_bytes_per_step": io_bytes,
         "steps": KE,
         "ms_per_m": {str(m): e2e_ms[m] for m in M_SWEEP},
+        # the value above is the mean over all steps; the median step shows the pipeline's own rate
+        # when a few steps are slowed by other work on the shared host
+        "median_step_ms": statistics.median(e2e_steps),
+        "max_step_ms": max(e2e_steps),
+        "median_value": bytes_step / (statistics.median(e2e_steps) * 1e-3) / 1e9,
         "api": "ens_gspmv_host (pinned host X/Y)",
     }
 
