@@ -339,8 +339,8 @@ ens_status ens_gspmv_host(ens_matrix *A, int32_t m, int32_t dtype, const void *X
     if (e != cudaSuccess) return cuda_fail(e, "gspmv_host");
     return ENS_OK;
   }
-  // Pipelined: X arrives in prefixes on one copy stream, each row chunk runs on `s` once the
-  // prefix it reads is in, and its Y rows leave on a second copy stream (both copy directions and
+  // Pipelined: X arrives in row blocks on one copy stream, each row chunk runs on `s` once the
+  // blocks it reads are in, and its Y rows leave on a second copy stream (both copy directions and
   // the kernels overlap).
   cudaError_t e = cudaSuccess;
   if (!A->pipe_h2d) {
