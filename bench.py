@@ -486,7 +486,7 @@ def cusparse_comparator(op, Xs, per_m_us, stream, reps: int = 20):
             ck(lib.cusparseCreateDnMat(ctypes.byref(dx), op.n, m, m, vp(X.data_ptr()), _CUDA_R_64F, _CUSPARSE_ORDER_ROW), "DnMat")
             ck(lib.cusparseCreateDnMat(ctypes.byref(dy), op.n, m, m, vp(Y.data_ptr()), _CUDA_R_64F, _CUSPARSE_ORDER_ROW), "DnMat")
             algs = _CUSPARSE_SPMM_ALGS
-        per_alg, best = {}, None
+        per_alg, best, best_y = {}, None, None
         for name, alg in algs.items():
             try:
                 size = ctypes.c_size_t(0)
@@ -518,10 +518,10 @@ def cusparse_comparator(op, Xs, per_m_us, stream, reps: int = 20):
                 e.record(stream)
                 torch.cuda.synchronize()
                 us = s.elapsed_time(e) / reps * 1e3
-                scale = torch.mm(absA, X.abs()) if m > 1 else torch.mv(absA, X.abs().reshape(-1)).reshape(-1, 1)
-                per_alg[name] = {"us": us, "Y": Y.clone(), "scale": scale}
+                per_alg[name] = {"us": us}
                 if best is None or us < per_alg[best]["us"]:
                     best = name
+                    best_y = Y.clone()  # the fastest algorithm's output, for the element-wise check
             except RuntimeError as exc:
                 per_alg[name] = {"unavailable": str(exc)}
         lib.cusparseDestroyDnMat(dx) if m > 1 else lib.cusparseDestroyDnVec(dx)
@@ -530,18 +530,16 @@ def cusparse_comparator(op, Xs, per_m_us, stream, reps: int = 20):
             out[str(m)] = {"unavailable": per_alg}
             continue
         us = per_alg[best]["us"]
+        scale = torch.mm(absA, X.abs()) if m > 1 else torch.mv(absA, X.abs().reshape(-1)).reshape(-1, 1)
         out[str(m)] = {
             "us": us,
             "algorithm": ("spmv_" if m == 1 else "spmm_") + best,
             "us_per_algorithm": {k: v.get("us") for k, v in per_alg.items()},
             "gbs": alg_bytes(op.n, op.nnz, m) / (us * 1e-6) / 1e9,
             "ours_speedup": us / per_m_us[m],
-            "Y": per_alg[best]["Y"],
-            "scale": per_alg[best]["scale"],
+            "Y": best_y,
+            "scale": scale,
         }
-        for v in per_alg.values():
-            v.pop("Y", None)
-            v.pop("scale", None)
     lib.cusparseDestroySpMat(A)
     lib.cusparseDestroy(h)
     return out
