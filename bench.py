@@ -163,13 +163,14 @@ def host_info():
     return {"nproc": os.cpu_count(), "model": model, "machine": os.uname().machine}
 
 
-def cpu_baseline_sweep(op, seconds_cap: float = 30.0):
+def cpu_baseline_sweep(op, seconds_cap: float = 30.0, reps: int = 10):
     """The oracle (C, FP64) on the host, as it stands: (i) the serial build on one core, column by
     column, one full m-sweep on the full channel operator (capped at `seconds_cap`); (ii) the OpenMP
     build of the same source on all host cores, column by column and with the columns of a row
-    together (the loop order of Fig. GSpMV), one full sweep each; (iii) the oracle's per-column
-    BiCGStab on the plain-method workload (32^3, m = 4, tol 1e-8), serial and all cores.
-    `value` is the fastest all-core product (GB/s of algorithmic bytes)."""
+    together (the loop order of Fig. GSpMV): 2 untimed sweeps, then the median of `reps` timed sweeps
+    (the row-wise one; the column-wise one, ~0.5 s a sweep, is capped at `seconds_cap` of timed
+    sweeps); (iii) the oracle's per-column BiCGStab on the plain-method workload (32^3, m = 4, tol
+    1e-8), serial and all cores. `value` is the faster all-core product (GB/s of algorithmic bytes)."""
     import gen
     import oracle
 
@@ -198,18 +199,30 @@ def cpu_baseline_sweep(op, seconds_cap: float = 30.0):
         "serial": {"gbs": serial_gbs, "cores": 1, "widths": serial_done},
         "host": host_info(),
     }
+    def median_sweeps(fn, cap=None):
+        for _ in range(2):
+            sweep(fn)
+        runs, spent = [], 0.0
+        while len(runs) < reps and (cap is None or spent < cap or len(runs) < 1):
+            gbs, _, t = sweep(fn)
+            runs.append(gbs)
+            spent += t
+        return statistics.median(runs), len(runs)
+
     if oracle.lib_omp() is not None:
         threads = oracle.threads(parallel=True)
-        col_gbs, _, _ = sweep(lambda X: oracle.gspmv(op, X, parallel=True))
-        row_gbs, _, _ = sweep(lambda X: oracle.gspmv_rowwise(op, X, parallel=True))
+        col_gbs, col_n = median_sweeps(lambda X: oracle.gspmv(op, X, parallel=True), seconds_cap)
+        row_gbs, row_n = median_sweeps(lambda X: oracle.gspmv_rowwise(op, X, parallel=True))
         out.update(
             {
                 "value": max(col_gbs, row_gbs),
                 "cores": threads,
-                "sample": f"one FP64 GSpMV per m in {list(M_SWEEP)} on the full {WORKLOAD} operator, OpenMP build of the "
-                f"oracle on {threads} threads (rows split; columns of a row together = {row_gbs:.2f} GB/s, column by column = "
-                f"{col_gbs:.2f} GB/s); the serial build on 1 core: {serial_gbs:.2f} GB/s",
-                "all_cores": {"threads": threads, "rowwise_gbs": row_gbs, "columnwise_gbs": col_gbs},
+                "sample": f"one FP64 GSpMV per m in {list(M_SWEEP)} on the full {WORKLOAD} operator per sweep, OpenMP build "
+                f"of the oracle on {threads} threads, median of {row_n} sweeps after 2 untimed ones (rows split; columns of a "
+                f"row together = {row_gbs:.2f} GB/s, column by column = {col_gbs:.2f} GB/s, median of {col_n}); the serial "
+                f"build on 1 core, one sweep: {serial_gbs:.2f} GB/s",
+                "all_cores": {"threads": threads, "rowwise_gbs": row_gbs, "columnwise_gbs": col_gbs,
+                              "rowwise_sweeps": row_n, "columnwise_sweeps": col_n},
             }
         )
     # oracle block solves: RHS-solves/s of the per-column BiCGStab on the plain-method workload
